@@ -1,0 +1,173 @@
+/*
+ * spgemm.h - C ABI of the GB300 (sm_103a) hash-based multi-phase SpGEMM.
+ *
+ * Computes C = A * B for sparse matrices in CSR form, following the three
+ * phases of arXiv 2512.12036 Section III: row grouping by intermediate
+ * products, the allocation (symbolic) phase that finds the structure of C,
+ * and the accumulation (numeric) phase that produces sorted, canonical rows.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All matrix arrays are DEVICE pointers on the plan's device. Indices are
+ *   int32, values fp32. Row r of a matrix occupies [row_ptr[r], row_ptr[r+1])
+ *   of col_idx/vals; row_ptr[0] need not be 0, so a block of rows of a larger
+ *   matrix can be passed as a view (row_ptr + r0, rows = r1 - r0) without
+ *   copying. spgemm_csr.nnz is the length of the col_idx/vals arrays.
+ * - Input rows may be unsorted and may repeat a column (repeats are summed).
+ *   Stored zeros are structure: an entry of C exists wherever some stored
+ *   a_ik meets some stored b_kj, whatever the values. Output rows are sorted
+ *   by column with no repeats.
+ * - The caller owns and allocates every device buffer, including the
+ *   workspace; nothing here calls cudaMalloc after spgemm_plan_create.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *   enqueued on it; an entry point only blocks the host where it says so.
+ * - Return value: SPGEMM_OK or one of the SPGEMM_ERR_* codes. Conditions the
+ *   kernels find on the device (an index out of range, a row_ptr that is not
+ *   monotone, an internal capacity guard) are recorded in a status word in
+ *   the workspace and reported by the next entry point that synchronises,
+ *   or by spgemm_status(). Kernels never fault or trap on bad input: they
+ *   skip the offending access and record the condition.
+ * - Value tolerance: every C value is within 1e-5 * sum_k |a_ik||b_kj| of
+ *   the exact result. Rows whose output entries can gather more than
+ *   opts.fp32_max_terms products accumulate in fp64 (the fp32 summation
+ *   bound gamma_t = t*2^-24 stays below 1e-5 only for t <= 167).
+ */
+#ifndef SPGEMM_H
+#define SPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SPGEMM_OK = 0,
+    SPGEMM_ERR_INVALID = 1,   /* null pointer, bad dimensions, bad row_ptr or index */
+    SPGEMM_ERR_WORKSPACE = 2, /* workspace missing or smaller than spgemm_workspace_bytes */
+    SPGEMM_ERR_OVERFLOW = 3,  /* result does not fit int32 row pointers: split A into row blocks */
+    SPGEMM_ERR_BUDGET = 4,    /* a memory budget given by the caller is exceeded */
+    SPGEMM_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+    SPGEMM_ERR_CUDA = 6,      /* a CUDA runtime call failed */
+    SPGEMM_ERR_INTERNAL = 7,  /* an internal capacity guard tripped (a bug) */
+    SPGEMM_ERR_UNSUPPORTED = 8 /* shape outside what the kernels handle */
+};
+
+/* CSR matrix view (device pointers). vals may be NULL where only structure is read. */
+typedef struct {
+    int32_t rows;
+    int32_t cols;
+    int64_t nnz;              /* length of col_idx / vals */
+    const int32_t* row_ptr;   /* rows + 1 */
+    const int32_t* col_idx;   /* nnz */
+    const float* vals;        /* nnz */
+} spgemm_csr;
+
+/* Tunables. Defaults come from spgemm_opts_default(); the row-group
+ * boundaries play the role of the paper's Table 1 (which fixes IP ranges
+ * 0-31 / 32-511 / 512-8191 / >=8192 for an H200) and are re-chosen for the
+ * GB300's 227 KB of shared memory per block. */
+typedef struct {
+    int32_t fp32_max_terms;   /* default 167: rows with more A entries accumulate in fp64 */
+    int32_t esc_max;          /* default 32: IP and A-row length bound of the in-register tier */
+    int32_t warp_max_ip;      /* default 1024: allocation phase, warp-per-row hash tier */
+    int32_t block_max_ip;     /* default 16384: allocation phase, block-per-row hash tier */
+    int32_t warp_max_nnz;     /* default 512: accumulation phase, warp-per-row hash tier */
+    int32_t block_max_nnz;    /* default 8192: accumulation phase, block-per-row hash tier */
+    int32_t panel_cols;       /* default 16384: column panel of the dense heavy-row accumulator */
+    int32_t reserved[9];
+} spgemm_opts;
+
+typedef struct spgemm_plan spgemm_plan;
+
+/* Fill opts with the defaults above. */
+int spgemm_opts_default(spgemm_opts* opts);
+
+/* Create a plan on CUDA device `device` (queries SM count and occupancy once).
+ * opts may be NULL for defaults. A plan holds no per-call state and may be
+ * shared by concurrent calls that use distinct workspaces. */
+int spgemm_plan_create(spgemm_plan** plan, const spgemm_opts* opts, int device);
+int spgemm_plan_destroy(spgemm_plan* plan);
+
+/* Bytes of workspace every phase below needs for these operand shapes
+ * (depends on A.rows, A.nnz, B.rows, B.cols only, never on values). */
+int spgemm_workspace_bytes(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                           size_t* bytes);
+
+/* Intermediate-product counting (Algorithm 1).
+ * ip_row   [out, device, A.rows int64]: IP_i = sum over stored (i,k) of |row k of B|.
+ * ip_total [out, host, nullable]: sum of ip_row; when non-NULL the call
+ *          synchronises the stream and also reports device-side errors.
+ * Requires A.cols == B.rows. Only the structure of A and B is read. */
+int spgemm_count(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, void* ws,
+                 size_t ws_bytes, int64_t* ip_row, int64_t* ip_total, void* stream);
+
+/* Row grouping (Section III-B): a stable partition of rows 0..n-1 by key
+ * into ngroups = nthr + 1 groups, group g holding thr[g-1] <= key < thr[g].
+ * map [out, device, n int32] lists the rows group by group, ascending row id
+ * inside a group; offsets [out, device, ngroups+1 int32]. nthr <= 32.
+ * key and thr are device int64 arrays. */
+int spgemm_group(const spgemm_plan* plan, const int64_t* key, int32_t n, const int64_t* thr,
+                 int32_t nthr, void* ws, size_t ws_bytes, int32_t* map, int32_t* offsets,
+                 void* stream);
+
+/* Allocation (symbolic) phase (Algorithms 2-4): the number of distinct
+ * columns of every row of C.
+ * ip_row    [in, device]: the output of spgemm_count for the same A and B.
+ * row_nnz   [out, device, A.rows int32].
+ * nnz_total [out, host, nullable]: int64 sum; non-NULL synchronises and
+ *           reports device-side errors.
+ * The workspace must stay untouched between this call and spgemm_numeric
+ * for the same A and B (it carries the allocation phase's state). */
+int spgemm_symbolic(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                    const int64_t* ip_row, void* ws, size_t ws_bytes, int32_t* row_nnz,
+                    int64_t* nnz_total, void* stream);
+
+/* Row pointers of C from the row counts (the rpt_C recurrence of
+ * Algorithms 2-3, computed as an exclusive scan).
+ * row_nnz [in, device, n], row_ptr [out, device, n+1] with row_ptr[0] = 0.
+ * total [out, host, nullable]: non-NULL synchronises; the call then returns
+ * SPGEMM_ERR_OVERFLOW when the sum exceeds INT32_MAX (row_ptr is then
+ * unspecified: pass a block of rows at a time instead). */
+int spgemm_row_ptr(const spgemm_plan* plan, const int32_t* row_nnz, int32_t n, void* ws,
+                   size_t ws_bytes, int32_t* row_ptr, int64_t* total, void* stream);
+
+/* Accumulation (numeric) phase with sorting (Algorithm 5 and the
+ * column-index sorting step): rows [row_begin, row_end) of C.
+ * ip_row    [in, device, A.rows]: from spgemm_count.
+ * row_ptr_C [in, device, row_end-row_begin+1]: row pointers of this block
+ *           of rows (row_ptr_C[0] = 0, e.g. spgemm_row_ptr on row_nnz + row_begin).
+ * col_C, val_C [out, device, row_ptr_C[last] entries].
+ * Does not synchronise; errors found on the device surface via spgemm_status. */
+int spgemm_numeric(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                   const int64_t* ip_row, int32_t row_begin, int32_t row_end,
+                   const int32_t* row_ptr_C, void* ws, size_t ws_bytes, int32_t* col_C,
+                   float* val_C, void* stream);
+
+/* Allocation callback for spgemm(): must return device buffers of nnz
+ * entries (col and val) and 0, or nonzero to abort. */
+typedef int (*spgemm_alloc_fn)(void* ctx, int64_t nnz, int32_t** col, float** val);
+
+/* The whole product in one call: count, symbolic, row pointers, alloc,
+ * numeric. ip_row and row_nnz are device scratch of A.rows entries each,
+ * row_ptr_C the device output of A.rows+1 entries. Synchronises twice (for
+ * the nnz of C and for the final status). *nnz_C receives the nnz of C.
+ * Returns SPGEMM_ERR_OVERFLOW (before allocating) when C needs more than
+ * INT32_MAX entries. */
+int spgemm(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, void* ws,
+           size_t ws_bytes, int64_t* ip_row, int32_t* row_nnz, int32_t* row_ptr_C,
+           spgemm_alloc_fn alloc, void* alloc_ctx, int64_t* nnz_C, void* stream);
+
+/* Synchronise `stream`, read and clear the workspace's device status word;
+ * *status receives the SPGEMM_ERR_* code it maps to (SPGEMM_OK if clean). */
+int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status);
+
+/* Short text for a status code. */
+const char* spgemm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPGEMM_H */

@@ -1,0 +1,272 @@
+"""Thin Python binding over the C ABI (argument marshalling only).
+
+PyTorch provides device memory and streams; every step of the SpGEMM runs
+in the CUDA kernels of libspgemm.so. Names follow the paper: intermediate
+products (IP, Algorithm 1), allocation phase (symbolic), accumulation phase
+(numeric).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import CsrStruct, OptsStruct, check
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+@dataclass
+class DeviceCSR:
+    """CSR matrix in device memory (int32 row_ptr/col, float32 val).
+
+    ``row_ptr[0]`` need not be 0: ``view_rows`` returns a block of rows that
+    shares the column and value arrays."""
+
+    rows: int
+    cols: int
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor | None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @property
+    def device(self) -> torch.device:
+        return self.row_ptr.device
+
+    @staticmethod
+    def from_host(A, device="cuda", non_blocking: bool = False) -> "DeviceCSR":
+        def up(a, dt):
+            t = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
+            if non_blocking:
+                t = t.pin_memory()
+            return t.to(device, non_blocking=non_blocking)
+        return DeviceCSR(A.rows, A.cols, up(A.row_ptr, np.int32), up(A.col, np.int32),
+                         up(A.val, np.float32))
+
+    def to_host(self):
+        from .gen import HostCSR
+        rp = self.row_ptr.cpu().numpy().astype(np.int64)
+        base = int(rp[0]) if rp.size else 0
+        end = int(rp[-1]) if rp.size else 0
+        col = self.col[base:end].cpu().numpy()
+        val = self.val[base:end].cpu().numpy() if self.val is not None else np.zeros(0, np.float32)
+        return HostCSR(self.rows, self.cols, (rp - base).astype(np.int32), col, val)
+
+    def view_rows(self, r0: int, r1: int) -> "DeviceCSR":
+        return DeviceCSR(r1 - r0, self.cols, self.row_ptr[r0:r1 + 1], self.col, self.val)
+
+    def struct(self) -> CsrStruct:
+        return CsrStruct(self.rows, self.cols, self.nnz, _ptr(self.row_ptr), _ptr(self.col),
+                         _ptr(self.val))
+
+
+def default_opts() -> dict:
+    o = OptsStruct()
+    check(_lib.lib().spgemm_opts_default(ctypes.byref(o)), "spgemm_opts_default")
+    return {n: getattr(o, n) for n in _lib.OPT_FIELDS}
+
+
+class Plan:
+    """An spgemm_plan on one device; stateless between calls."""
+
+    def __init__(self, device: int | None = None, **opts):
+        L = _lib.lib()
+        o = OptsStruct()
+        check(L.spgemm_opts_default(ctypes.byref(o)), "spgemm_opts_default")
+        for k, v in opts.items():
+            if k not in _lib.OPT_FIELDS:
+                raise KeyError(k)
+            setattr(o, k, int(v))
+        self.opts = {n: getattr(o, n) for n in _lib.OPT_FIELDS}
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        h = ctypes.c_void_p()
+        check(L.spgemm_plan_create(ctypes.byref(h), ctypes.byref(o), device), "spgemm_plan_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _lib.lib().spgemm_plan_destroy(h)
+            self.handle = None
+
+    # ----------------------------------------------------------------- helpers
+    def workspace_bytes(self, A: DeviceCSR, B: DeviceCSR) -> int:
+        n = ctypes.c_size_t()
+        check(_lib.lib().spgemm_workspace_bytes(self.handle, ctypes.byref(A.struct()),
+                                                ctypes.byref(B.struct()), ctypes.byref(n)),
+              "spgemm_workspace_bytes")
+        return int(n.value)
+
+    def workspace(self, A: DeviceCSR, B: DeviceCSR) -> torch.Tensor:
+        nbytes = self.workspace_bytes(A, B)
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=A.device)
+        off = (-ws.data_ptr()) % 256
+        return ws[off:off + nbytes]
+
+    # ------------------------------------------------------------------ phases
+    def count(self, A: DeviceCSR, B: DeviceCSR, ws: torch.Tensor, ip_row: torch.Tensor | None = None,
+              total: bool = True, stream=None):
+        """Algorithm 1: int64 IP per row (device) and, if ``total``, the int64 sum."""
+        if ip_row is None:
+            ip_row = torch.empty(A.rows, dtype=torch.int64, device=A.device)
+        t = ctypes.c_int64()
+        check(_lib.lib().spgemm_count(self.handle, ctypes.byref(A.struct()), ctypes.byref(B.struct()),
+                                      _ptr(ws), ws.numel(), _ptr(ip_row),
+                                      ctypes.byref(t) if total else None, _stream(stream)),
+              "spgemm_count")
+        return ip_row, (int(t.value) if total else None)
+
+    def group(self, key: torch.Tensor, thresholds, ws: torch.Tensor, stream=None):
+        """Section III-B grouping of ``key`` (device int64) at ``thresholds``."""
+        thr = torch.as_tensor(list(thresholds), dtype=torch.int64, device=key.device)
+        n = key.numel()
+        mp = torch.empty(n, dtype=torch.int32, device=key.device)
+        off = torch.empty(thr.numel() + 2, dtype=torch.int32, device=key.device)
+        check(_lib.lib().spgemm_group(self.handle, _ptr(key), n, _ptr(thr), thr.numel(), _ptr(ws),
+                                      ws.numel(), _ptr(mp), _ptr(off), _stream(stream)),
+              "spgemm_group")
+        return mp, off
+
+    def symbolic(self, A: DeviceCSR, B: DeviceCSR, ip_row: torch.Tensor, ws: torch.Tensor,
+                 row_nnz: torch.Tensor | None = None, total: bool = True, stream=None):
+        """Allocation phase: int32 nnz per row of C and (if ``total``) the int64 sum."""
+        if row_nnz is None:
+            row_nnz = torch.empty(A.rows, dtype=torch.int32, device=A.device)
+        t = ctypes.c_int64()
+        check(_lib.lib().spgemm_symbolic(self.handle, ctypes.byref(A.struct()),
+                                         ctypes.byref(B.struct()), _ptr(ip_row), _ptr(ws),
+                                         ws.numel(), _ptr(row_nnz),
+                                         ctypes.byref(t) if total else None, _stream(stream)),
+              "spgemm_symbolic")
+        return row_nnz, (int(t.value) if total else None)
+
+    def row_ptr(self, row_nnz: torch.Tensor, ws: torch.Tensor, out: torch.Tensor | None = None,
+                total: bool = False, stream=None):
+        n = row_nnz.numel()
+        if out is None:
+            out = torch.empty(n + 1, dtype=torch.int32, device=row_nnz.device)
+        t = ctypes.c_int64()
+        check(_lib.lib().spgemm_row_ptr(self.handle, _ptr(row_nnz), n, _ptr(ws), ws.numel(),
+                                        _ptr(out), ctypes.byref(t) if total else None,
+                                        _stream(stream)),
+              "spgemm_row_ptr")
+        return out, (int(t.value) if total else None)
+
+    def numeric(self, A: DeviceCSR, B: DeviceCSR, ip_row: torch.Tensor, row_ptr_C: torch.Tensor,
+                ws: torch.Tensor, col_C: torch.Tensor, val_C: torch.Tensor, row_begin: int = 0,
+                row_end: int | None = None, stream=None) -> None:
+        """Accumulation phase for rows [row_begin, row_end) into col_C/val_C."""
+        if row_end is None:
+            row_end = A.rows
+        check(_lib.lib().spgemm_numeric(self.handle, ctypes.byref(A.struct()),
+                                        ctypes.byref(B.struct()), _ptr(ip_row), row_begin, row_end,
+                                        _ptr(row_ptr_C), _ptr(ws), ws.numel(), _ptr(col_C),
+                                        _ptr(val_C), _stream(stream)),
+              "spgemm_numeric")
+
+    def status(self, ws: torch.Tensor, stream=None) -> int:
+        st = ctypes.c_int()
+        check(_lib.lib().spgemm_status(self.handle, _ptr(ws), _stream(stream), ctypes.byref(st)),
+              "spgemm_status")
+        return int(st.value)
+
+    def check_status(self, ws: torch.Tensor, where: str = "device", stream=None) -> None:
+        check(self.status(ws, stream), where)
+
+    # ------------------------------------------------------------ whole product
+    def spgemm(self, A: DeviceCSR, B: DeviceCSR, ws: torch.Tensor | None = None,
+               stream=None) -> DeviceCSR:
+        """C = A*B through the one-call entry point (C allocated by torch)."""
+        if ws is None:
+            ws = self.workspace(A, B)
+        dev = A.device
+        ip_row = torch.empty(A.rows, dtype=torch.int64, device=dev)
+        row_nnz = torch.empty(A.rows, dtype=torch.int32, device=dev)
+        row_ptr = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+        keep = {}
+
+        def alloc(ctx, nnz, colp, valp):
+            keep["col"] = torch.empty(int(nnz), dtype=torch.int32, device=dev)
+            keep["val"] = torch.empty(int(nnz), dtype=torch.float32, device=dev)
+            colp[0] = _ptr(keep["col"])
+            valp[0] = _ptr(keep["val"])
+            return 0
+
+        cb = _lib.ALLOC_FN(alloc)
+        nnz = ctypes.c_int64()
+        check(_lib.lib().spgemm(self.handle, ctypes.byref(A.struct()), ctypes.byref(B.struct()),
+                                _ptr(ws), ws.numel(), _ptr(ip_row), _ptr(row_nnz), _ptr(row_ptr),
+                                cb, None, ctypes.byref(nnz), _stream(stream)),
+              "spgemm")
+        return DeviceCSR(A.rows, B.cols, row_ptr, keep["col"], keep["val"])
+
+    def spgemm_blocks(self, A: DeviceCSR, B: DeviceCSR, max_block_nnz: int = 2**31 - 1,
+                      ws: torch.Tensor | None = None, stream=None, out=None):
+        """C = A*B as blocks of consecutive rows, each with int32 row pointers and
+        at most ``max_block_nnz`` entries (for results beyond 2^31-1 entries).
+
+        Returns (blocks, ip_total, nnz_total) with blocks a list of
+        (row_begin, row_end, DeviceCSR). ``out`` may give preallocated blocks
+        from an earlier call with the same operands."""
+        if ws is None:
+            ws = self.workspace(A, B)
+        ip_row, ip_total = self.count(A, B, ws, stream=stream)
+        row_nnz, nnz_total = self.symbolic(A, B, ip_row, ws, stream=stream)
+        bounds = split_rows(row_nnz, max_block_nnz)
+        blocks = []
+        for q, (r0, r1) in enumerate(bounds):
+            if out is not None:
+                _, _, Cq = out[q]
+                rp = Cq.row_ptr
+            else:
+                rp = None
+            rp, tot = self.row_ptr(row_nnz[r0:r1], ws, out=rp, total=out is None, stream=stream)
+            if out is not None:
+                col, val = Cq.col, Cq.val
+            else:
+                col = torch.empty(tot, dtype=torch.int32, device=A.device)
+                val = torch.empty(tot, dtype=torch.float32, device=A.device)
+            self.numeric(A, B, ip_row, rp, ws, col, val, r0, r1, stream=stream)
+            blocks.append((r0, r1, DeviceCSR(r1 - r0, B.cols, rp, col, val)))
+        return blocks, ip_total, nnz_total
+
+
+def split_rows(row_nnz: torch.Tensor, max_block_nnz: int):
+    """Consecutive row ranges whose nnz sums stay <= max_block_nnz (host-side
+    planning from the per-row counts of the allocation phase)."""
+    counts = row_nnz.to(torch.int64).cpu().numpy()
+    n = counts.shape[0]
+    if n == 0:
+        return [(0, 0)]
+    if counts.max(initial=0) > max_block_nnz:
+        raise ValueError("a single row exceeds the block limit")
+    csum = np.cumsum(counts)
+    bounds = []
+    r0 = 0
+    base = 0
+    while r0 < n:
+        r1 = int(np.searchsorted(csum, base + max_block_nnz, side="right"))
+        r1 = max(r1, r0 + 1)
+        bounds.append((r0, r1))
+        base = int(csum[r1 - 1])
+        r0 = r1
+    return bounds

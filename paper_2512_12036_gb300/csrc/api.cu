@@ -1,0 +1,336 @@
+// C ABI of libspgemm: argument checks, workspace layout and phase order.
+#include <stdlib.h>
+#include <string.h>
+
+#include "internal.h"
+
+namespace spg {
+void occupancy_symbolic(spgemm_plan* p);
+void occupancy_numeric(spgemm_plan* p);
+void launch_bpanel(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaStream_t s);
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long long b_cols) {
+    WsLayout L;
+    L.m = (int)m;
+    L.nblk = (int)((m + kBinRows - 1) / kBinRows);
+    L.nscan = (int)((m + kScanItems - 1) / kScanItems);
+    const long long pw = p->opts.panel_cols;
+    L.panels = (int)((b_cols + pw - 1) / pw);
+    size_t off = 0;
+    L.ctl = off;
+    off = align256(off + sizeof(Ctl));
+    L.map = off;
+    off = align256(off + sizeof(int) * (size_t)(m > 0 ? m : 1));
+    L.blk_counts = off;
+    off = align256(off + sizeof(int) * (size_t)kNumBins * (size_t)(L.nblk > 0 ? L.nblk : 1));
+    L.scan_part = off;
+    off = align256(off + sizeof(long long) * (size_t)(L.nscan + 1));
+    L.bpanel = off;
+    if (L.panels > 0 && L.panels <= kMaxPanels && b_rows > 0)
+        off = align256(off + sizeof(int) * (size_t)b_rows * (size_t)(L.panels + 1));
+    L.total = off;
+    return L;
+}
+
+WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols) {
+    char* b = (char*)ws;
+    WsPtrs w;
+    w.ctl = (Ctl*)(b + L.ctl);
+    w.map = (int*)(b + L.map);
+    w.blk_counts = (int*)(b + L.blk_counts);
+    w.scan_part = (long long*)(b + L.scan_part);
+    w.bpanel = L.total > L.bpanel ? (int*)(b + L.bpanel) : nullptr;
+    w.nblk = L.nblk;
+    w.nscan = L.nscan;
+    w.panels = L.panels;
+    w.panel_cols = panel_cols;
+    return w;
+}
+
+void init_occupancy(spgemm_plan* p) {
+    occupancy_symbolic(p);
+    occupancy_numeric(p);
+}
+
+}  // namespace spg
+
+using namespace spg;
+
+static int cuda_err(cudaError_t e) { return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA; }
+
+static int check_csr(const spgemm_csr* M, bool need_vals) {
+    if (!M) return SPGEMM_ERR_INVALID;
+    if (M->rows < 0 || M->cols < 0 || M->nnz < 0 || M->nnz > 2147483647ll) return SPGEMM_ERR_INVALID;
+    if (!M->row_ptr) return SPGEMM_ERR_INVALID;
+    if (M->nnz > 0 && !M->col_idx) return SPGEMM_ERR_INVALID;
+    if (need_vals && M->nnz > 0 && !M->vals) return SPGEMM_ERR_INVALID;
+    return SPGEMM_OK;
+}
+
+static CsrDev dev_view(const spgemm_csr* M) {
+    CsrDev d;
+    d.rows = M->rows;
+    d.cols = M->cols;
+    d.nnz = M->nnz;
+    d.rpt = M->row_ptr;
+    d.col = M->col_idx;
+    d.val = M->vals;
+    return d;
+}
+
+static int check_pair(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                      bool need_vals) {
+    if (!plan) return SPGEMM_ERR_INVALID;
+    int rc = check_csr(A, need_vals);
+    if (rc) return rc;
+    rc = check_csr(B, need_vals);
+    if (rc) return rc;
+    if (A->cols != B->rows) return SPGEMM_ERR_INVALID;
+    return SPGEMM_OK;
+}
+
+static int check_ws(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, void* ws,
+                    size_t ws_bytes, WsLayout* L) {
+    *L = ws_layout(plan, A->rows, B->rows, B->cols);
+    if (!ws || ws_bytes < L->total) return SPGEMM_ERR_WORKSPACE;
+    if (((uintptr_t)ws & 255) != 0) return SPGEMM_ERR_WORKSPACE;
+    return SPGEMM_OK;
+}
+
+static int map_status(int bits) {
+    if (bits & ST_INVALID) return SPGEMM_ERR_INVALID;
+    if (bits & ST_OVERFLOW) return SPGEMM_ERR_OVERFLOW;
+    if (bits & ST_TIMEOUT) return SPGEMM_ERR_TIMEOUT;
+    if (bits & ST_UNSUPPORTED) return SPGEMM_ERR_UNSUPPORTED;
+    if (bits & ST_INTERNAL) return SPGEMM_ERR_INTERNAL;
+    return SPGEMM_OK;
+}
+
+// Synchronise, fetch totals[which] (if out) and the status word, clear it.
+static int sync_read(Ctl* ctl, int which, int64_t* out, cudaStream_t s) {
+    struct {
+        int status;
+        int pad[3];
+        long long totals[8];
+    } h;
+    cudaError_t e = cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return SPGEMM_ERR_CUDA;
+    if (out && which >= 0) *out = h.totals[which];
+    if (h.status) {
+        int zero = 0;
+        cudaMemcpyAsync(&ctl->status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+    }
+    return map_status(h.status);
+}
+
+extern "C" {
+
+int spgemm_opts_default(spgemm_opts* o) {
+    if (!o) return SPGEMM_ERR_INVALID;
+    memset(o, 0, sizeof(*o));
+    o->fp32_max_terms = 167;
+    o->esc_max = 32;
+    o->warp_max_ip = 1024;
+    o->block_max_ip = 16384;
+    o->warp_max_nnz = 512;
+    o->block_max_nnz = 8192;
+    o->panel_cols = 16384;
+    return SPGEMM_OK;
+}
+
+int spgemm_plan_create(spgemm_plan** out, const spgemm_opts* opts, int device) {
+    if (!out) return SPGEMM_ERR_INVALID;
+    *out = nullptr;
+    spgemm_opts o;
+    if (opts) o = *opts;
+    else spgemm_opts_default(&o);
+    // limits of the kernels: in-register tier is one warp, tables are powers
+    // of two in shared memory, a dense panel is at most 32 columns per thread
+    if (o.esc_max < 1 || o.esc_max > 32) return SPGEMM_ERR_INVALID;
+    if (o.warp_max_ip < o.esc_max || o.warp_max_ip > kWarpTableSym / 2) return SPGEMM_ERR_INVALID;
+    if (o.block_max_ip < o.warp_max_ip || o.block_max_ip > 32768) return SPGEMM_ERR_INVALID;
+    if (o.warp_max_nnz < 1 || o.warp_max_nnz > kWarpTableNum / 2) return SPGEMM_ERR_INVALID;
+    if (o.block_max_nnz < o.warp_max_nnz || o.block_max_nnz > 8192) return SPGEMM_ERR_INVALID;
+    if (o.panel_cols < 1024 || o.panel_cols > 32 * kNumDenseThreads || (o.panel_cols & 31))
+        return SPGEMM_ERR_INVALID;
+    if (o.fp32_max_terms < 0) return SPGEMM_ERR_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return SPGEMM_ERR_CUDA;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    spgemm_plan* p = (spgemm_plan*)calloc(1, sizeof(spgemm_plan));
+    if (!p) return SPGEMM_ERR_INTERNAL;
+    p->device = device;
+    p->opts = o;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    p->num_sms = v > 0 ? v : 1;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    p->smem_optin = (size_t)v;
+    init_occupancy(p);
+    cudaError_t e = cudaGetLastError();
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        free(p);
+        return SPGEMM_ERR_CUDA;
+    }
+    *out = p;
+    return SPGEMM_OK;
+}
+
+int spgemm_plan_destroy(spgemm_plan* p) {
+    free(p);
+    return SPGEMM_OK;
+}
+
+int spgemm_workspace_bytes(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                           size_t* bytes) {
+    if (!plan || !A || !B || !bytes) return SPGEMM_ERR_INVALID;
+    if (A->rows < 0 || B->rows < 0 || B->cols < 0) return SPGEMM_ERR_INVALID;
+    *bytes = ws_layout(plan, A->rows, B->rows, B->cols).total;
+    return SPGEMM_OK;
+}
+
+int spgemm_count(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, void* ws,
+                 size_t ws_bytes, int64_t* ip_row, int64_t* ip_total, void* stream) {
+    int rc = check_pair(plan, A, B, false);
+    if (rc) return rc;
+    if (A->rows > 0 && !ip_row) return SPGEMM_ERR_INVALID;
+    WsLayout L;
+    rc = check_ws(plan, A, B, ws, ws_bytes, &L);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    launch_ip_count(plan, dev_view(A), dev_view(B), (long long*)ip_row, w, s);
+    rc = cuda_err(cudaGetLastError());
+    if (rc) return rc;
+    if (ip_total) return sync_read(w.ctl, 0, ip_total, s);
+    return SPGEMM_OK;
+}
+
+int spgemm_group(const spgemm_plan* plan, const int64_t* key, int32_t n, const int64_t* thr,
+                 int32_t nthr, void* ws, size_t ws_bytes, int32_t* map, int32_t* offsets,
+                 void* stream) {
+    if (!plan || n < 0 || nthr < 0 || nthr > 32 || !offsets) return SPGEMM_ERR_INVALID;
+    if (n > 0 && (!key || !map)) return SPGEMM_ERR_INVALID;
+    if (nthr > 0 && !thr) return SPGEMM_ERR_INVALID;
+    WsLayout L = ws_layout(plan, n, 0, 0);
+    if (!ws || ws_bytes < L.total || ((uintptr_t)ws & 255)) return SPGEMM_ERR_WORKSPACE;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    GroupArgs g{};
+    g.phase = 2;
+    g.n = n;
+    g.key = (const long long*)key;
+    g.thr = (const long long*)thr;
+    g.nthr = nthr;
+    g.opts = plan->opts;
+    launch_group(plan, g, w, map, offsets, (cudaStream_t)stream);
+    return cuda_err(cudaGetLastError());
+}
+
+int spgemm_symbolic(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                    const int64_t* ip_row, void* ws, size_t ws_bytes, int32_t* row_nnz,
+                    int64_t* nnz_total, void* stream) {
+    int rc = check_pair(plan, A, B, false);
+    if (rc) return rc;
+    if (A->rows > 0 && (!ip_row || !row_nnz)) return SPGEMM_ERR_INVALID;
+    WsLayout L;
+    rc = check_ws(plan, A, B, ws, ws_bytes, &L);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    CsrDev dA = dev_view(A), dB = dev_view(B);
+    launch_symbolic(plan, dA, dB, (const long long*)ip_row, w, row_nnz, s);
+    launch_bpanel(plan, dB, w, s);
+    launch_nnz_total(row_nnz, A->rows, w, s);
+    rc = cuda_err(cudaGetLastError());
+    if (rc) return rc;
+    if (nnz_total) return sync_read(w.ctl, 1, nnz_total, s);
+    return SPGEMM_OK;
+}
+
+int spgemm_row_ptr(const spgemm_plan* plan, const int32_t* row_nnz, int32_t n, void* ws,
+                   size_t ws_bytes, int32_t* row_ptr, int64_t* total, void* stream) {
+    if (!plan || n < 0 || !row_ptr || (n > 0 && !row_nnz)) return SPGEMM_ERR_INVALID;
+    WsLayout L = ws_layout(plan, n, 0, 0);
+    if (!ws || ws_bytes < L.total || ((uintptr_t)ws & 255)) return SPGEMM_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    launch_row_ptr(plan, row_nnz, n, w, row_ptr, s);
+    int rc = cuda_err(cudaGetLastError());
+    if (rc) return rc;
+    if (total) return sync_read(w.ctl, 2, total, s);
+    return SPGEMM_OK;
+}
+
+int spgemm_numeric(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                   const int64_t* ip_row, int32_t row_begin, int32_t row_end,
+                   const int32_t* row_ptr_C, void* ws, size_t ws_bytes, int32_t* col_C,
+                   float* val_C, void* stream) {
+    int rc = check_pair(plan, A, B, true);
+    if (rc) return rc;
+    if (row_begin < 0 || row_end < row_begin || row_end > A->rows) return SPGEMM_ERR_INVALID;
+    if (row_end > row_begin && (!ip_row || !row_ptr_C)) return SPGEMM_ERR_INVALID;
+    WsLayout L;
+    rc = check_ws(plan, A, B, ws, ws_bytes, &L);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    launch_numeric(plan, dev_view(A), dev_view(B), (const long long*)ip_row, row_begin, row_end,
+                   row_ptr_C, w, col_C, val_C, s);
+    return cuda_err(cudaGetLastError());
+}
+
+int spgemm(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, void* ws,
+           size_t ws_bytes, int64_t* ip_row, int32_t* row_nnz, int32_t* row_ptr_C,
+           spgemm_alloc_fn alloc, void* alloc_ctx, int64_t* nnz_C, void* stream) {
+    int rc = check_pair(plan, A, B, true);
+    if (rc) return rc;
+    if (!alloc || !nnz_C || !row_ptr_C) return SPGEMM_ERR_INVALID;
+    rc = spgemm_count(plan, A, B, ws, ws_bytes, ip_row, nullptr, stream);
+    if (rc) return rc;
+    int64_t total = 0;
+    rc = spgemm_symbolic(plan, A, B, ip_row, ws, ws_bytes, row_nnz, &total, stream);
+    if (rc) return rc;
+    *nnz_C = total;
+    if (total > 2147483647ll) return SPGEMM_ERR_OVERFLOW;
+    rc = spgemm_row_ptr(plan, row_nnz, A->rows, ws, ws_bytes, row_ptr_C, nullptr, stream);
+    if (rc) return rc;
+    int32_t* col = nullptr;
+    float* val = nullptr;
+    if (alloc(alloc_ctx, total, &col, &val) != 0) return SPGEMM_ERR_BUDGET;
+    if (total > 0 && (!col || !val)) return SPGEMM_ERR_BUDGET;
+    rc = spgemm_numeric(plan, A, B, ip_row, 0, A->rows, row_ptr_C, ws, ws_bytes, col, val, stream);
+    if (rc) return rc;
+    WsLayout L = ws_layout(plan, A->rows, B->rows, B->cols);
+    return sync_read(ws_ptrs(L, ws, plan->opts.panel_cols).ctl, -1, nullptr, (cudaStream_t)stream);
+}
+
+int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status) {
+    if (!plan || !ws || !status) return SPGEMM_ERR_INVALID;
+    *status = sync_read((Ctl*)ws, -1, nullptr, (cudaStream_t)stream);
+    return *status == SPGEMM_ERR_CUDA ? SPGEMM_ERR_CUDA : SPGEMM_OK;
+}
+
+const char* spgemm_status_string(int st) {
+    switch (st) {
+        case SPGEMM_OK: return "ok";
+        case SPGEMM_ERR_INVALID: return "invalid argument or malformed CSR input";
+        case SPGEMM_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case SPGEMM_ERR_OVERFLOW: return "result exceeds int32 row pointers; split A into row blocks";
+        case SPGEMM_ERR_BUDGET: return "memory budget exceeded or allocation refused";
+        case SPGEMM_ERR_TIMEOUT: return "bounded device wait gave up";
+        case SPGEMM_ERR_CUDA: return "CUDA runtime error";
+        case SPGEMM_ERR_INTERNAL: return "internal capacity guard tripped";
+        case SPGEMM_ERR_UNSUPPORTED: return "unsupported shape";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Host-side internals of libspgemm: plan, workspace layout, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/spgemm.h"
+#include "common.cuh"
+
+struct spgemm_plan {
+    int device;
+    int num_sms;
+    size_t smem_optin;     // max dynamic shared memory per block
+    spgemm_opts opts;
+    // resident blocks per SM for each persistent kernel (filled at creation)
+    int occ_sym_warp, occ_sym_block, occ_sym_dense;
+    int occ_num_warp32, occ_num_warp64, occ_num_block32, occ_num_block64;
+    int occ_num_dense32, occ_num_dense64;
+};
+
+namespace spg {
+
+constexpr int kBinRows = 1024;      // rows per block in the grouping kernels
+constexpr int kScanItems = 4096;    // rows per block in the row-pointer scan
+constexpr int kWarpTableSym = 2048; // keys per warp, allocation warp tier
+constexpr int kWarpsPerBlockSW = 8;
+constexpr int kWarpTableNum = 1024; // entries per warp, accumulation warp tier
+constexpr int kWarpsPerBlockNW = 8;
+constexpr int kSymBlockThreads = 512;
+constexpr int kSymDenseThreads = 1024;
+constexpr int kNumBlockThreads = 512;
+constexpr int kNumDenseThreads = 1024;
+constexpr int kMaxPanels = 1024;    // above this the heavy path filters whole B rows
+
+// Bins (phase-specific meaning). Allocation phase:
+//   0: in-register tier, 1: warp hash, 2..5: block hash (by log2 IP, heavy
+//   first), 6..37: dense bitmap (by log2 IP, heavy first), 63: nothing to do.
+// Accumulation phase:
+//   0: in-register tier, 1/2: warp hash fp32/fp64, 3/4: block hash fp32/fp64,
+//   5..20: dense panels fp32, 21..36: dense panels fp64 (by log2 IP, heavy
+//   first), 63: nothing to do.
+enum : int {
+    SB_ESC = 0, SB_WARP = 1, SB_BLOCK0 = 2, SB_BLOCK_N = 4, SB_DENSE0 = 6, SB_DENSE_N = 32,
+    NB_ESC = 0, NB_WARP32 = 1, NB_WARP64 = 2, NB_BLOCK32 = 3, NB_BLOCK64 = 4,
+    NB_DENSE32_0 = 5, NB_DENSE_N = 16, NB_DENSE64_0 = 21
+};
+
+// Workspace layout: all offsets 256-byte aligned, derived from shapes only.
+struct WsLayout {
+    size_t ctl = 0;          // Ctl
+    size_t map = 0;          // int32 [m]
+    size_t blk_counts = 0;   // int32 [kNumBins][nblk]
+    size_t scan_part = 0;    // int64 [nscan + 1]
+    size_t bpanel = 0;       // int32 [B.rows][P+1]  (0 bytes when P > kMaxPanels)
+    size_t total = 0;
+    int m = 0, nblk = 0, nscan = 0, panels = 0;
+};
+
+WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long long b_cols);
+
+struct WsPtrs {
+    Ctl* ctl;
+    int* map;
+    int* blk_counts;
+    long long* scan_part;
+    int* bpanel;
+    int nblk, nscan, panels, panel_cols;
+};
+
+WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols);
+
+// Launchers (stream-ordered, no host synchronisation).
+void launch_fill_i64(long long* p, long long n, long long v, cudaStream_t s);
+void launch_ip_count(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, long long* ip,
+                     const WsPtrs& w, cudaStream_t s);
+
+// Grouping: phase 0 = allocation, 1 = accumulation, 2 = generic thresholds.
+struct GroupArgs {
+    int phase;
+    int row_begin, n;          // rows [row_begin, row_begin + n) of A
+    const long long* ip;       // indexed by absolute row
+    const int* rptA;           // A row pointers (absolute rows)
+    const int* rptC;           // accumulation: block-relative row pointers of C
+    int* row_nnz;              // allocation: rows settled during grouping (IP <= 1)
+    const long long* key;      // generic: keys (n)
+    const long long* thr;      // generic: thresholds
+    int nthr;
+    spgemm_opts opts;
+};
+void launch_group(const spgemm_plan* p, const GroupArgs& g, const WsPtrs& w, int* map_out,
+                  int* offsets_out, cudaStream_t s);
+
+void launch_row_ptr(const spgemm_plan* p, const int* row_nnz, int n, const WsPtrs& w,
+                    int* row_ptr, cudaStream_t s);
+
+void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
+                     const WsPtrs& w, int* row_nnz, cudaStream_t s);
+void launch_nnz_total(const int* row_nnz, int n, const WsPtrs& w, cudaStream_t s);
+
+void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
+                    int row_begin, int row_end, const int* rptC, const WsPtrs& w, int* colC,
+                    float* valC, cudaStream_t s);
+
+void init_occupancy(spgemm_plan* p);
+
+}  // namespace spg

@@ -1,0 +1,504 @@
+// Accumulation (numeric) phase with compaction and column sort
+// (Algorithm 5, element gathering and column-index sorting steps).
+//
+// Row tiers (bins by the row's nnz, IP and A-row length):
+//   ESC   IP <= 32: one warp, one product per lane; equal columns summed in
+//         a fixed lane order and ranked by comparison, written sorted.
+//   WARP  nnz <= 512: warp per row, (key, value) table in shared memory
+//         (Algorithm 4's AddInTable), then in-place compaction and a bitonic
+//         sort of the occupied slots.
+//   BLOCK nnz <= 8192: block per row, same scheme with a block-wide table.
+//   DENSE larger rows: block per row, a dense accumulator over one column
+//         panel at a time (values + occupancy bitmap in shared memory). The
+//         B entries of a panel are found through a per-B-row panel offset
+//         table, so each product is read once; the bitmap is scanned in
+//         column order, which emits the row already sorted (no sort step).
+// Accumulators are fp32 where a row's A length keeps every output entry at
+// <= fp32_max_terms products, fp64 otherwise.
+#include "internal.h"
+
+namespace spg {
+
+template <typename Acc>
+__device__ __forceinline__ void hash_add(int* keys, Acc* vals, int bits, int key, Acc v, Ctl* ctl) {
+    const unsigned mask = (1u << bits) - 1u;
+    unsigned h = hash_slot(key, bits);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        const int cur = *(volatile int*)&keys[h];
+        if (cur == key) {
+            atomicAdd(&vals[h], v);
+            return;
+        }
+        if (cur == kEmpty) {
+            const int old = atomicCAS(&keys[h], kEmpty, key);
+            if (old == kEmpty || old == key) {
+                atomicAdd(&vals[h], v);
+                return;
+            }
+        }
+        h = (h + 1u) & mask;
+    }
+    set_status(ctl, ST_INTERNAL);
+}
+
+__device__ __forceinline__ bool key_in(int key, const CsrDev& B, Ctl* ctl) {
+    if ((unsigned)key >= (unsigned)B.cols) {
+        set_status(ctl, ST_INVALID);
+        return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_num_esc(CsrDev A, CsrDev B, const int* map, Ctl* ctl,
+                                                 const int* rptC, int row_begin, int* colC,
+                                                 float* valC, int bin) {
+    const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int idx = begin + gw; idx < end; idx += nw) {
+        const int r = map[idx];
+        const int row = row_begin + r;
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        int bs = 0, len = 0;
+        float a = 0.f;
+        if (rs + lane < re) {
+            a_entry(A, B, rs + lane, bs, len, ctl);
+            a = A.val[rs + lane];
+        }
+        const int incl = warp_incl_scan(len);
+        const int excl = incl - len;
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int s = warp_find_src(excl, lane);
+        const int sbs = __shfl_sync(kFull, bs, s);
+        const int sex = __shfl_sync(kFull, excl, s);
+        const float sa = __shfl_sync(kFull, a, s);
+        int key = -1;
+        float prod = 0.f;
+        if (lane < total) {
+            const int t = sbs + lane - sex;
+            key = B.col[t];
+            if (key_in(key, B, ctl)) prod = sa * B.val[t];
+            else key = -1;
+        }
+        const unsigned peers = __match_any_sync(kFull, key);
+        const int leader = (key >= 0 && (peers & lanemask_lt()) == 0) ? 1 : 0;
+        float sum = 0.f;
+        int rank = 0;
+        for (int q = 0; q < 32; ++q) {
+            const int kq = __shfl_sync(kFull, key, q);
+            const float vq = __shfl_sync(kFull, prod, q);
+            const int lq = __shfl_sync(kFull, leader, q);
+            if (kq == key) sum += vq;
+            if (lq && kq < key) ++rank;
+        }
+        const int out = rptC[r];
+        const int nnz_row = rptC[r + 1] - out;
+        const int distinct = __popc(__ballot_sync(kFull, leader));
+        if (lane == 0 && (distinct != nnz_row || total > 32)) set_status(ctl, ST_INTERNAL);
+        if (leader && rank < nnz_row) {
+            colC[out + rank] = key;
+            valC[out + rank] = sum;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bitonic sort of n2 (power of two) (key, value) pairs in shared memory,
+// ascending by key, by `nthreads` cooperating threads starting at `tid`.
+template <typename Acc, bool kBlock>
+__device__ __forceinline__ void bitonic_sort(int* keys, Acc* vals, int n2, int tid, int nthreads) {
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < n2; i += nthreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const int ki = keys[i], kj = keys[ixj];
+                    const bool asc = (i & k) == 0;
+                    if ((ki > kj) == asc) {
+                        keys[i] = kj;
+                        keys[ixj] = ki;
+                        const Acc t = vals[i];
+                        vals[i] = vals[ixj];
+                        vals[ixj] = t;
+                    }
+                }
+            }
+            if (kBlock) __syncthreads();
+            else __syncwarp();
+        }
+    }
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(kWarpsPerBlockNW * 32) k_num_warp(CsrDev A, CsrDev B,
+                                                                    const int* map, Ctl* ctl,
+                                                                    const int* rptC, int row_begin,
+                                                                    int* colC, float* valC,
+                                                                    int bin) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    Acc* vals = reinterpret_cast<Acc*>(sm_raw) + warp * kWarpTableNum;
+    int* keys = reinterpret_cast<int*>(sm_raw + sizeof(Acc) * kWarpsPerBlockNW * kWarpTableNum) +
+                warp * kWarpTableNum;
+    const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    constexpr int kMaxBits = 10;
+    for (int idx = begin + gw; idx < end; idx += nw) {
+        const int r = map[idx];
+        const int row = row_begin + r;
+        const int out = rptC[r];
+        const int nnz_row = rptC[r + 1] - out;
+        int bits = 5;
+        while (bits < kMaxBits && (1 << bits) < 2 * nnz_row) ++bits;
+        const int T = 1 << bits;
+        for (int t = lane; t < T; t += 32) {
+            keys[t] = kEmpty;
+            vals[t] = Acc(0);
+        }
+        __syncwarp();
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        warp_expand(A, B, rs, re, 32, ctl, [&](int t, int ja) {
+            const int key = B.col[t];
+            if (key_in(key, B, ctl))
+                hash_add<Acc>(keys, vals, bits, key, (Acc)A.val[ja] * (Acc)B.val[t], ctl);
+        });
+        __syncwarp();
+        int n = 0;
+        for (int c = 0; c < T; c += 32) {
+            const int k = keys[c + lane];
+            const Acc v = vals[c + lane];
+            const bool occ = k != kEmpty;
+            const unsigned bal = __ballot_sync(kFull, occ);
+            const int pos = n + __popc(bal & lanemask_lt());
+            __syncwarp();
+            if (occ) {
+                keys[pos] = k;
+                vals[pos] = v;
+            }
+            n += __popc(bal);
+            __syncwarp();
+        }
+        if (lane == 0 && n != nnz_row) set_status(ctl, ST_INTERNAL);
+        const int nn = n < nnz_row ? n : nnz_row;
+        const int n2 = (int)pow2_ceil((unsigned)(nn > 1 ? nn : 1));
+        for (int t = nn + lane; t < n2; t += 32) keys[t] = 0x7fffffff;
+        __syncwarp();
+        bitonic_sort<Acc, false>(keys, vals, n2, lane, 32);
+        for (int t = lane; t < nn; t += 32) {
+            colC[out + t] = keys[t];
+            valC[out + t] = (float)vals[t];
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <typename Acc>
+__global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev B,
+                                                                const int* map, Ctl* ctl,
+                                                                const int* rptC, int row_begin,
+                                                                int* colC, float* valC, int bin,
+                                                                int tier, int max_bits) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    Acc* vals = reinterpret_cast<Acc*>(sm_raw);
+    int* keys = reinterpret_cast<int*>(sm_raw + sizeof(Acc) * (1u << max_bits));
+    __shared__ int s_idx;
+    __shared__ int scratch[33];
+    const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= end) break;
+        const int r = map[idx];
+        const int row = row_begin + r;
+        const int out = rptC[r];
+        const int nnz_row = rptC[r + 1] - out;
+        int bits = 6;
+        while (bits < max_bits && (1 << bits) < 2 * nnz_row) ++bits;
+        const int T = 1 << bits;
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            keys[t] = kEmpty;
+            vals[t] = Acc(0);
+        }
+        __syncthreads();
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        warp_expand(A, B, rs + warp * 32, re, 32 * nwarps, ctl, [&](int t, int ja) {
+            const int key = B.col[t];
+            if (key_in(key, B, ctl))
+                hash_add<Acc>(keys, vals, bits, key, (Acc)A.val[ja] * (Acc)B.val[t], ctl);
+        });
+        __syncthreads();
+        // stable in-place compaction, 4 slots per thread per round
+        int n = 0;
+        const int per_round = blockDim.x * 4;
+        for (int base = 0; base < T; base += per_round) {
+            int k[4];
+            Acc v[4];
+            int cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int slot = base + threadIdx.x * 4 + q;
+                k[q] = slot < T ? keys[slot] : kEmpty;
+                v[q] = slot < T ? vals[slot] : Acc(0);
+                cnt += k[q] != kEmpty;
+            }
+            int tot;
+            int pos = n + block_excl_scan(cnt, scratch, &tot);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (k[q] != kEmpty) {
+                    keys[pos] = k[q];
+                    vals[pos] = v[q];
+                    ++pos;
+                }
+            }
+            n += tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && n != nnz_row) set_status(ctl, ST_INTERNAL);
+        const int nn = n < nnz_row ? n : nnz_row;
+        const int n2 = (int)pow2_ceil((unsigned)(nn > 1 ? nn : 1));
+        for (int t = nn + threadIdx.x; t < n2; t += blockDim.x) keys[t] = 0x7fffffff;
+        __syncthreads();
+        bitonic_sort<Acc, true>(keys, vals, n2, threadIdx.x, blockDim.x);
+        for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+            colC[out + t] = keys[t];
+            valC[out + t] = (float)vals[t];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Panel offset table of B: for row k and panel p, tab[k*(P+1)+p] is the
+// first position of row k whose column is >= p*PW (valid when rows are
+// sorted; an unsorted row sets ctl->b_unsorted and the dense tier then
+// filters whole B rows instead).
+__global__ void k_bpanel(CsrDev B, int P, int PW, int* tab, Ctl* ctl) {
+    const int lane = lane_id();
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = gw; k < B.rows; k += nw) {
+        int s, e;
+        if (!row_extent(B, (int)k, s, e, ctl)) {
+            for (int p = lane; p <= P; p += 32) tab[k * (P + 1) + p] = 0;
+            continue;
+        }
+        bool unsorted = false;
+        for (int t = s + lane; t <= e; t += 32) {
+            int prev = -1, cur = P;
+            if (t > s) {
+                const int c = B.col[t - 1];
+                prev = c < 0 ? 0 : (c / PW >= P ? P - 1 : c / PW);
+            }
+            if (t < e) {
+                const int c = B.col[t];
+                cur = c < 0 ? 0 : (c / PW >= P ? P - 1 : c / PW);
+                if (t > s && c < B.col[t - 1]) unsorted = true;
+            }
+            for (int p = prev + 1; p <= cur; ++p) tab[k * (P + 1) + p] = t;
+        }
+        if (__any_sync(kFull, unsorted) && lane == 0) atomicExch(&ctl->b_unsorted, 1);
+    }
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(kNumDenseThreads) k_num_dense(CsrDev A, CsrDev B,
+                                                                const int* map, Ctl* ctl,
+                                                                const int* rptC, int row_begin,
+                                                                int* colC, float* valC, int bin_lo,
+                                                                int bin_hi, int tier,
+                                                                const int* tab, int P, int PW) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    Acc* vals = reinterpret_cast<Acc*>(sm_raw);
+    unsigned* bm = reinterpret_cast<unsigned*>(sm_raw + sizeof(Acc) * PW);
+    __shared__ int s_idx;
+    __shared__ int scratch[33];
+    const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
+    if (begin >= end) return;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nwords_pw = PW >> 5;
+    for (int i = threadIdx.x; i < PW; i += blockDim.x) vals[i] = Acc(0);
+    for (int i = threadIdx.x; i < nwords_pw; i += blockDim.x) bm[i] = 0u;
+    const bool use_tab = tab != nullptr && ctl->b_unsorted == 0;
+    const int npanels = (int)((B.cols + (long long)PW - 1) / PW);
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= end) break;
+        const int r = map[idx];
+        const int row = row_begin + r;
+        const int out = rptC[r];
+        const int nnz_row = rptC[r + 1] - out;
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        int written = 0;
+        for (int p = 0; p < npanels; ++p) {
+            const int c0 = p * PW;
+            const int span = (int)(B.cols - (long long)c0 < PW ? B.cols - (long long)c0 : PW);
+            // products of this panel
+            const int lane = lane_id();
+            for (int base = rs + warp * 32; base < re; base += 32 * nwarps) {
+                const int j = base + lane;
+                int bs = 0, len = 0;
+                Acc a = Acc(0);
+                if (j < re) {
+                    a_entry(A, B, j, bs, len, ctl);
+                    a = (Acc)A.val[j];
+                    if (use_tab && len > 0) {
+                        const int k = A.col[j];
+                        const int* tk = tab + (long long)k * (P + 1);
+                        const int ps = tk[p], pe = tk[p + 1];
+                        if (ps >= bs && pe >= ps && pe <= bs + len) {
+                            bs = ps;
+                            len = pe - ps;
+                        } else {
+                            set_status(ctl, ST_INTERNAL);
+                            len = 0;
+                        }
+                    }
+                }
+                const int incl = warp_incl_scan(len);
+                const int excl = incl - len;
+                const int total = __shfl_sync(kFull, incl, 31);
+                for (int p0 = 0; p0 < total; p0 += 32) {
+                    const int pp = p0 + lane;
+                    const int s = warp_find_src(excl, pp);
+                    const int sbs = __shfl_sync(kFull, bs, s);
+                    const int sex = __shfl_sync(kFull, excl, s);
+                    const Acc sa = __shfl_sync(kFull, a, s);
+                    if (pp < total) {
+                        const int t = sbs + (pp - sex);
+                        const int key = B.col[t];
+                        if (key_in(key, B, ctl)) {
+                            const int kk = key - c0;
+                            if (kk >= 0 && kk < span) {
+                                const unsigned bit = 1u << (kk & 31);
+                                unsigned* wp = &bm[kk >> 5];
+                                if (!(*(volatile unsigned*)wp & bit)) atomicOr(wp, bit);
+                                atomicAdd(&vals[kk], sa * (Acc)B.val[t]);
+                            } else if (use_tab) {
+                                set_status(ctl, ST_INTERNAL);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // emit this panel in column order
+            const int nw = (span + 31) >> 5;
+            const unsigned word = (int)threadIdx.x < nw ? bm[threadIdx.x] : 0u;
+            int tot;
+            int pos = written + block_excl_scan(__popc(word), scratch, &tot);
+            if ((int)threadIdx.x < nw) {
+                unsigned wbits = word;
+                while (wbits) {
+                    const int b = __ffs(wbits) - 1;
+                    wbits &= wbits - 1;
+                    const int kk = threadIdx.x * 32 + b;
+                    const Acc v = vals[kk];
+                    vals[kk] = Acc(0);
+                    if (pos < nnz_row) {
+                        colC[out + pos] = c0 + kk;
+                        valC[out + pos] = (float)v;
+                    }
+                    ++pos;
+                }
+                bm[threadIdx.x] = 0u;
+            }
+            written += tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && written != nnz_row) set_status(ctl, ST_INTERNAL);
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+static size_t num_warp_smem(size_t acc) { return (acc + 4) * kWarpsPerBlockNW * kWarpTableNum; }
+static size_t num_block_smem(const spgemm_plan* p, size_t acc) {
+    return (acc + 4) * pow2_ceil(2u * (unsigned)p->opts.block_max_nnz);
+}
+static size_t num_dense_smem(const spgemm_plan* p, size_t acc) {
+    return acc * p->opts.panel_cols + p->opts.panel_cols / 8;
+}
+
+void occupancy_numeric(spgemm_plan* p) {
+    struct K {
+        const void* f;
+        int threads;
+        size_t smem;
+        int* occ;
+    } ks[] = {
+        {(const void*)k_num_warp<float>, kWarpsPerBlockNW * 32, num_warp_smem(4), &p->occ_num_warp32},
+        {(const void*)k_num_warp<double>, kWarpsPerBlockNW * 32, num_warp_smem(8), &p->occ_num_warp64},
+        {(const void*)k_num_block<float>, kNumBlockThreads, num_block_smem(p, 4), &p->occ_num_block32},
+        {(const void*)k_num_block<double>, kNumBlockThreads, num_block_smem(p, 8), &p->occ_num_block64},
+        {(const void*)k_num_dense<float>, kNumDenseThreads, num_dense_smem(p, 4), &p->occ_num_dense32},
+        {(const void*)k_num_dense<double>, kNumDenseThreads, num_dense_smem(p, 8), &p->occ_num_dense64},
+    };
+    for (auto& k : ks) {
+        cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(k.occ, k.f, k.threads, k.smem);
+        if (*k.occ < 1) *k.occ = 1;
+    }
+}
+
+__global__ void k_reset_bflag(Ctl* ctl) { ctl->b_unsorted = 0; }
+
+void launch_bpanel(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaStream_t s) {
+    k_reset_bflag<<<1, 1, 0, s>>>(w.ctl);
+    if (w.bpanel == nullptr || B.rows == 0) return;
+    const long long warps = B.rows;
+    long long blocks = (warps * 32 + 255) / 256;
+    if (blocks > (long long)p->num_sms * 16) blocks = (long long)p->num_sms * 16;
+    k_bpanel<<<(int)blocks, 256, 0, s>>>(B, w.panels, w.panel_cols, w.bpanel, w.ctl);
+}
+
+void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
+                    int row_begin, int row_end, const int* rptC, const WsPtrs& w, int* colC,
+                    float* valC, cudaStream_t s) {
+    GroupArgs g{};
+    g.phase = 1;
+    g.row_begin = row_begin;
+    g.n = row_end - row_begin;
+    g.ip = ip;
+    g.rptA = A.rpt;
+    g.rptC = rptC;
+    g.opts = p->opts;
+    launch_group(p, g, w, w.map, nullptr, s);
+    if (g.n == 0) return;
+    const int sms = p->num_sms;
+    k_num_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_ESC);
+    k_num_warp<float><<<sms * p->occ_num_warp32, kWarpsPerBlockNW * 32, num_warp_smem(4), s>>>(
+        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP32);
+    k_num_warp<double><<<sms * p->occ_num_warp64, kWarpsPerBlockNW * 32, num_warp_smem(8), s>>>(
+        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP64);
+    const unsigned tb = pow2_ceil(2u * (unsigned)p->opts.block_max_nnz);
+    int max_bits = 0;
+    while ((1u << max_bits) < tb) ++max_bits;
+    k_num_block<float><<<sms * p->occ_num_block32, kNumBlockThreads, num_block_smem(p, 4), s>>>(
+        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK32, 2, max_bits);
+    k_num_block<double><<<sms * p->occ_num_block64, kNumBlockThreads, num_block_smem(p, 8), s>>>(
+        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits);
+    const int PW = w.panel_cols;
+    k_num_dense<float><<<sms * p->occ_num_dense32, kNumDenseThreads, num_dense_smem(p, 4), s>>>(
+        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0, NB_DENSE32_0 + NB_DENSE_N,
+        4, w.bpanel, w.panels, PW);
+    k_num_dense<double><<<sms * p->occ_num_dense64, kNumDenseThreads, num_dense_smem(p, 8), s>>>(
+        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0, NB_DENSE64_0 + NB_DENSE_N,
+        5, w.bpanel, w.panels, PW);
+}
+
+}  // namespace spg

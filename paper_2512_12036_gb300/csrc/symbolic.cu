@@ -1,0 +1,247 @@
+// Allocation (symbolic) phase: nnz of every row of C (Algorithms 2-4).
+//
+// Row tiers (bins from the grouping phase):
+//   ESC   IP <= 32 and |A_i| <= 32: one warp, one product per lane; distinct
+//         columns counted with __match_any_sync, no table at all.
+//   WARP  IP <= 1024: one warp per row, open-addressing table of keys in
+//         shared memory (Algorithm 4's InsertIntoTable), sized 2*IP.
+//   BLOCK IP <= 16384: one block per row, shared table sized 2*IP.
+//   DENSE larger rows: one block per row, a bitmap over the columns in
+//         shared memory (192 KB = 1.5M columns per pass); every product is a
+//         single atomicOr and nnz is a popcount, so no row ever overflows a
+//         table and no global-memory table is needed.
+#include "internal.h"
+
+namespace spg {
+
+constexpr int kSymDenseWords = 48 * 1024;   // 192 KB bitmap
+
+__device__ __forceinline__ int hash_insert(int* table, int bits, int key, Ctl* ctl) {
+    const unsigned mask = (1u << bits) - 1u;
+    unsigned h = hash_slot(key, bits);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        const int cur = *(volatile int*)&table[h];
+        if (cur == key) return 0;
+        if (cur == kEmpty) {
+            const int old = atomicCAS(&table[h], kEmpty, key);
+            if (old == kEmpty) return 1;
+            if (old == key) return 0;
+        }
+        h = (h + 1u) & mask;
+    }
+    set_status(ctl, ST_INTERNAL);
+    return 0;
+}
+
+__device__ __forceinline__ bool key_ok(int key, const CsrDev& B, Ctl* ctl) {
+    if ((unsigned)key >= (unsigned)B.cols) {
+        set_status(ctl, ST_INVALID);
+        return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sym_esc(CsrDev A, CsrDev B, const int* map, Ctl* ctl,
+                                                 int* row_nnz, int bin) {
+    const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int idx = begin + gw; idx < end; idx += nw) {
+        const int row = map[idx];
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        int bs = 0, len = 0;
+        if (rs + lane < re) a_entry(A, B, rs + lane, bs, len, ctl);
+        const int incl = warp_incl_scan(len);
+        const int excl = incl - len;
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int s = warp_find_src(excl, lane);
+        const int sbs = __shfl_sync(kFull, bs, s);
+        const int sex = __shfl_sync(kFull, excl, s);
+        int key = -1;
+        if (lane < total) {
+            key = B.col[sbs + lane - sex];
+            if (!key_ok(key, B, ctl)) key = -1;
+        }
+        const unsigned peers = __match_any_sync(kFull, key);
+        const bool first = key >= 0 && (peers & lanemask_lt()) == 0;
+        const int nnz = __popc(__ballot_sync(kFull, first));
+        if (lane == 0) {
+            if (total > 32 || re - rs > 32) set_status(ctl, ST_INTERNAL);
+            row_nnz[row] = nnz;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWarpsPerBlockSW * 32) k_sym_warp(CsrDev A, CsrDev B,
+                                                                    const long long* ip,
+                                                                    const int* map, Ctl* ctl,
+                                                                    int* row_nnz, int bin) {
+    extern __shared__ int sm_tables[];
+    int* table = sm_tables + (threadIdx.x >> 5) * kWarpTableSym;
+    const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    constexpr int kMaxBits = 11;   // 2048 slots
+    for (int idx = begin + gw; idx < end; idx += nw) {
+        const int row = map[idx];
+        const long long want = 2 * ip[row];
+        int bits = 5;
+        while (bits < kMaxBits && (1ll << bits) < want) ++bits;
+        const int T = 1 << bits;
+        for (int t = lane; t < T; t += 32) table[t] = kEmpty;
+        __syncwarp();
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        int cnt = 0;
+        warp_expand(A, B, rs, re, 32, ctl, [&](int t, int) {
+            const int key = B.col[t];
+            if (key_ok(key, B, ctl)) cnt += hash_insert(table, bits, key, ctl);
+        });
+        cnt = warp_sum(cnt);
+        if (lane == 0) row_nnz[row] = cnt;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev B,
+                                                                const long long* ip,
+                                                                const int* map, Ctl* ctl,
+                                                                int* row_nnz, int bin_lo,
+                                                                int bin_hi, int tier,
+                                                                int max_bits) {
+    extern __shared__ int table[];
+    __shared__ int s_idx;
+    __shared__ int red[33];
+    const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= end) break;
+        const int row = map[idx];
+        const long long want = 2 * ip[row];
+        int bits = 6;
+        while (bits < max_bits && (1ll << bits) < want) ++bits;
+        const int T = 1 << bits;
+        for (int t = threadIdx.x; t < T; t += blockDim.x) table[t] = kEmpty;
+        __syncthreads();
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        int cnt = 0;
+        warp_expand(A, B, rs + warp * 32, re, 32 * nwarps, ctl, [&](int t, int) {
+            const int key = B.col[t];
+            if (key_ok(key, B, ctl)) cnt += hash_insert(table, bits, key, ctl);
+        });
+        cnt = block_sum(cnt, red);
+        if (threadIdx.x == 0) row_nnz[row] = cnt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSymDenseThreads) k_sym_dense(CsrDev A, CsrDev B,
+                                                                const int* map, Ctl* ctl,
+                                                                int* row_nnz, int bin_lo,
+                                                                int bin_hi, int tier,
+                                                                int nwords) {
+    extern __shared__ unsigned bm[];
+    __shared__ int s_idx;
+    __shared__ int red[33];
+    const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const long long span_max = (long long)nwords * 32;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= end) break;
+        const int row = map[idx];
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        int nnz = 0;
+        for (long long c0 = 0; c0 < B.cols; c0 += span_max) {
+            const int span = (int)(B.cols - c0 < span_max ? B.cols - c0 : span_max);
+            const int nw = (span + 31) >> 5;
+            for (int q = threadIdx.x; q < nw; q += blockDim.x) bm[q] = 0u;
+            __syncthreads();
+            warp_expand(A, B, rs + warp * 32, re, 32 * nwarps, ctl, [&](int t, int) {
+                const int key = B.col[t];
+                if (!key_ok(key, B, ctl)) return;
+                const long long kk = key - c0;
+                if (kk < 0 || kk >= span) return;
+                const unsigned bit = 1u << (kk & 31);
+                unsigned* wp = &bm[kk >> 5];
+                if (!(*(volatile unsigned*)wp & bit)) atomicOr(wp, bit);
+            });
+            __syncthreads();
+            int cnt = 0;
+            for (int q = threadIdx.x; q < nw; q += blockDim.x) cnt += __popc(bm[q]);
+            nnz += block_sum(cnt, red);
+        }
+        if (threadIdx.x == 0) row_nnz[row] = nnz;
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+static size_t sym_dense_smem(const spgemm_plan* p) {
+    size_t words = kSymDenseWords;
+    const size_t cap = (p->smem_optin > 4096 ? p->smem_optin - 2048 : 4096) / 4;
+    if (words > cap) words = cap;
+    return words * 4;
+}
+
+void occupancy_symbolic(spgemm_plan* p) {
+    const size_t sw = (size_t)kWarpsPerBlockSW * kWarpTableSym * 4;
+    const size_t sb = (size_t)pow2_ceil(2u * (unsigned)p->opts.block_max_ip) * 4;
+    const size_t sd = sym_dense_smem(p);
+    cudaFuncSetAttribute(k_sym_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw);
+    cudaFuncSetAttribute(k_sym_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    cudaFuncSetAttribute(k_sym_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_warp, k_sym_warp,
+                                                  kWarpsPerBlockSW * 32, sw);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block, k_sym_block,
+                                                  kSymBlockThreads, sb);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_dense, k_sym_dense,
+                                                  kSymDenseThreads, sd);
+    if (p->occ_sym_warp < 1) p->occ_sym_warp = 1;
+    if (p->occ_sym_block < 1) p->occ_sym_block = 1;
+    if (p->occ_sym_dense < 1) p->occ_sym_dense = 1;
+}
+
+void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
+                     const WsPtrs& w, int* row_nnz, cudaStream_t s) {
+    GroupArgs g{};
+    g.phase = 0;
+    g.row_begin = 0;
+    g.n = A.rows;
+    g.ip = ip;
+    g.rptA = A.rpt;
+    g.row_nnz = row_nnz;
+    g.opts = p->opts;
+    launch_group(p, g, w, w.map, nullptr, s);
+    if (A.rows == 0) return;
+    const int sms = p->num_sms;
+    k_sym_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, row_nnz, SB_ESC);
+    const size_t sw = (size_t)kWarpsPerBlockSW * kWarpTableSym * 4;
+    k_sym_warp<<<sms * p->occ_sym_warp, kWarpsPerBlockSW * 32, sw, s>>>(A, B, ip, w.map, w.ctl,
+                                                                       row_nnz, SB_WARP);
+    const unsigned tb = pow2_ceil(2u * (unsigned)p->opts.block_max_ip);
+    int max_bits = 0;
+    while ((1u << max_bits) < tb) ++max_bits;
+    k_sym_block<<<sms * p->occ_sym_block, kSymBlockThreads, (size_t)tb * 4, s>>>(
+        A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, SB_BLOCK0 + SB_BLOCK_N, 0, max_bits);
+    const size_t sd = sym_dense_smem(p);
+    k_sym_dense<<<sms * p->occ_sym_dense, kSymDenseThreads, sd, s>>>(
+        A, B, w.map, w.ctl, row_nnz, SB_DENSE0, SB_DENSE0 + SB_DENSE_N, 1, (int)(sd / 4));
+}
+
+}  // namespace spg

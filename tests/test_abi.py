@@ -1,0 +1,30 @@
+"""CPU-only checks of the C ABI: the library builds for sm_103a, loads, and
+exports every function that include/spgemm.h declares."""
+import ctypes
+
+from paper_2512_12036_gb300 import _lib
+
+
+def test_header_symbols_exported():
+    L = _lib.lib()
+    names = _lib.header_symbols()
+    assert "spgemm_numeric" in names and "spgemm_count" in names
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in _lib.PROTOTYPES, f"{n} has no ctypes prototype"
+
+
+def test_status_strings_and_defaults():
+    L = _lib.lib()
+    for code in range(0, 9):
+        assert L.spgemm_status_string(code)
+    o = _lib.OptsStruct()
+    assert L.spgemm_opts_default(ctypes.byref(o)) == 0
+    assert o.fp32_max_terms == 167 and o.esc_max == 32
+
+
+def test_invalid_arguments_rejected_without_gpu():
+    L = _lib.lib()
+    assert L.spgemm_plan_create(None, None, 0) == _lib.ERR_INVALID
+    n = ctypes.c_size_t()
+    assert L.spgemm_workspace_bytes(None, None, None, ctypes.byref(n)) == _lib.ERR_INVALID

@@ -1,0 +1,214 @@
+"""GPU parity: every phase of the CUDA path against the CPU oracle, through
+the C ABI, on seeded inputs that reach every row tier (in-register, warp
+hash, block hash, dense panels; fp32 and fp64 accumulation), several tiles
+and ragged tails, plus empty and malformed inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2512_12036_gb300 import DeviceCSR, Plan, SpgemmError, gen
+from paper_2512_12036_gb300 import _lib
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def plan():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return Plan()
+
+
+def run(plan, A, B):
+    dA, dB = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
+    C = plan.spgemm(dA, dB)
+    torch.cuda.synchronize()
+    return C.to_host()
+
+
+def check_product(plan, A, B):
+    got = run(plan, A, B)
+    ref = oracle.spgemm(A, B)
+    return compare(got, ref)
+
+
+def hub_matrix(rows, cols, seed, heavy_rows, heavy_len, light_deg=4):
+    """Rows with ``light_deg`` random columns, plus heavy rows of ``heavy_len``."""
+    rng = np.random.default_rng(seed)
+    r, c = [], []
+    for i in range(rows):
+        d = heavy_len if i in heavy_rows else rng.integers(0, light_deg + 1)
+        cc = rng.choice(cols, size=min(d, cols), replace=False)
+        r.append(np.full(cc.size, i))
+        c.append(cc)
+    r = np.concatenate(r)
+    c = np.concatenate(c)
+    return gen.csr_from_coo(rows, cols, r, c, gen.uniform_open_closed(rng, r.size))
+
+
+def test_er4096_self_product(plan):
+    A = gen.erdos_renyi(4096, 8, seed=1)
+    check_product(plan, A, A)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_rmat_small_skewed(plan, seed):
+    A = gen.rmat_symmetric(12, 16, seed=seed)
+    check_product(plan, A, A)
+
+
+@pytest.mark.parametrize("kind", ["plain", "duplicates", "unsorted", "zeros_signed"])
+def test_random_shapes(plan, kind):
+    kw = {"plain": {}, "duplicates": {"duplicates": True}, "unsorted": {"unsorted": True},
+          "zeros_signed": {"explicit_zeros": 0.3, "signed": True}}[kind]
+    A = gen.random_csr(300, 200, 0.03, 11, **kw)
+    B = gen.random_csr(200, 500, 0.05, 12, **kw)
+    check_product(plan, A, B)
+
+
+def test_every_tier(plan):
+    # B: 40k columns (3 dense panels, ragged tail); rows of B of varied length
+    B = hub_matrix(3000, 40000, 5, heavy_rows=set(range(0, 3000, 7)), heavy_len=300, light_deg=12)
+    # A: light rows (in-register / warp), medium rows (block), heavy rows
+    # (dense panels) incl. rows with > 167 entries (fp64 accumulation)
+    A = hub_matrix(700, 3000, 6, heavy_rows={1, 50, 51, 300, 699}, heavy_len=900, light_deg=40)
+    ip, _ = oracle.ip_count(A, B)
+    nnz = oracle.symbolic(A, B)
+    assert ip.max() > 16384 and (ip <= 32).sum() > 0 and ((ip > 1024) & (ip <= 16384)).sum() > 0
+    assert nnz.max() > 8192 and ((nnz > 512) & (nnz <= 8192)).sum() > 0
+    check_product(plan, A, B)
+
+
+def test_dense_tier_unsorted_b(plan):
+    B = hub_matrix(500, 50000, 7, heavy_rows=set(range(0, 500, 3)), heavy_len=400)
+    Bu = gen.random_csr(1, 1, 1.0, 0)  # placeholder for type
+    rng = np.random.default_rng(1)
+    col, val = B.col.copy(), B.val.copy()
+    for i in range(B.rows):
+        s, e = B.row_ptr[i], B.row_ptr[i + 1]
+        p = rng.permutation(e - s) + s
+        col[s:e], val[s:e] = col[p], val[p]
+    Bu = gen.HostCSR(B.rows, B.cols, B.row_ptr, col, val)
+    A = hub_matrix(50, 500, 8, heavy_rows={0, 10, 20}, heavy_len=300)
+    assert oracle.symbolic(A, Bu).max() > 8192
+    check_product(plan, A, Bu)
+
+
+def test_all_products_one_column(plan):
+    # every product of row 0 lands in column 3: nnz 1, IP 20000 (contended slot)
+    k = 20000
+    B = gen.HostCSR(k, 10, np.arange(k + 1, dtype=np.int32), np.full(k, 3, np.int32),
+                    np.full(k, 0.5, np.float32))
+    A = gen.HostCSR(2, k, np.array([0, k, k + 5], np.int32),
+                    np.concatenate([np.arange(k), np.arange(5)]).astype(np.int32),
+                    np.ones(k + 5, np.float32))
+    check_product(plan, A, B)
+
+
+def test_hash_collisions(plan):
+    # columns that are multiples of 2^16 and consecutive runs
+    cols = np.concatenate([np.arange(0, 2**16 * 30, 2**16), np.arange(100, 900)])
+    n = cols.max() + 1
+    B = gen.csr_from_coo(3, int(n), np.repeat(np.arange(3), cols.size), np.tile(cols, 3),
+                         np.ones(3 * cols.size, np.float32))
+    A = gen.HostCSR(1, 3, np.array([0, 3], np.int32), np.arange(3, dtype=np.int32),
+                    np.array([1, 2, 3], np.float32))
+    check_product(plan, A, B)
+
+
+def test_empty_inputs(plan):
+    B = gen.random_csr(5, 6, 0.5, seed=3)
+    Z = gen.HostCSR(4, 5, np.zeros(5, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    got = run(plan, Z, B)
+    assert got.nnz == 0 and got.row_ptr.tolist() == [0] * 5
+    E = gen.HostCSR(0, 5, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    got = run(plan, E, B)
+    assert got.rows == 0 and got.nnz == 0
+    one = gen.HostCSR(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32),
+                      np.array([2.0], np.float32))
+    got = run(plan, one, one)
+    assert got.col.tolist() == [0] and got.val.tolist() == [4.0]
+
+
+def test_phases_individually(plan):
+    A = gen.rmat_symmetric(11, 8, seed=5)
+    dA = DeviceCSR.from_host(A)
+    ws = plan.workspace(dA, dA)
+    ip, total = plan.count(dA, dA, ws)
+    ip_ref, total_ref = oracle.ip_count(A, A)
+    assert total == total_ref and np.array_equal(ip.cpu().numpy(), ip_ref)
+    nnz, nnz_total = plan.symbolic(dA, dA, ip, ws)
+    nnz_ref = oracle.symbolic(A, A)
+    assert np.array_equal(nnz.cpu().numpy(), nnz_ref) and nnz_total == int(nnz_ref.sum())
+    rp, tot = plan.row_ptr(nnz, ws, total=True)
+    assert tot == int(nnz_ref.sum())
+    assert np.array_equal(rp.cpu().numpy()[1:], np.cumsum(nnz_ref)) and int(rp[0]) == 0
+    mp, off = plan.group(ip, [32, 512, 8192], ws)
+    mp_ref, off_ref = oracle.group_rows(ip_ref, [32, 512, 8192])
+    assert np.array_equal(mp.cpu().numpy(), mp_ref) and np.array_equal(off.cpu().numpy(), off_ref)
+
+
+def test_row_ptr_overflow_detected(plan):
+    dA = DeviceCSR.from_host(gen.erdos_renyi(64, 4, seed=2))
+    ws = plan.workspace(dA, dA)
+    counts = torch.tensor([2**30, 2**30, 2**30], dtype=torch.int32, device="cuda")
+    with pytest.raises(SpgemmError) as e:
+        plan.row_ptr(counts, ws, total=True)
+    assert e.value.code == _lib.ERR_OVERFLOW
+
+
+def test_row_blocks_equal_whole(plan):
+    A = gen.rmat_symmetric(11, 8, seed=6)
+    dA = DeviceCSR.from_host(A)
+    blocks, ip_total, nnz_total = plan.spgemm_blocks(dA, dA, max_block_nnz=20000)
+    assert len(blocks) > 3
+    ref = oracle.spgemm(A, A)
+    assert nnz_total == ref.nnz and ip_total == oracle.ip_count(A, A)[1]
+    for r0, r1, Cb in blocks:
+        h = Cb.to_host()
+        sub = oracle.OracleCSR(r1 - r0, A.cols, ref.row_ptr[r0:r1 + 1] - ref.row_ptr[r0],
+                               ref.col[ref.row_ptr[r0]:ref.row_ptr[r1]],
+                               ref.val[ref.row_ptr[r0]:ref.row_ptr[r1]],
+                               ref.bound[ref.row_ptr[r0]:ref.row_ptr[r1]])
+        compare(h, sub)
+
+
+def test_row_view_input(plan):
+    A = gen.erdos_renyi(1000, 10, seed=4)
+    dA = DeviceCSR.from_host(A)
+    V = dA.view_rows(300, 700)
+    C = plan.spgemm(V, dA).to_host()
+    ref = oracle.spgemm(A, A, rows=np.arange(300, 700, dtype=np.int32))
+    compare(C, ref)
+
+
+def test_structure_deterministic(plan):
+    A = gen.rmat_symmetric(12, 8, seed=8)
+    c1 = run(plan, A, A)
+    c2 = run(plan, A, A)
+    assert np.array_equal(c1.row_ptr, c2.row_ptr) and np.array_equal(c1.col, c2.col)
+
+
+@pytest.mark.parametrize("what", ["a_col", "b_col", "a_rowptr"])
+def test_malformed_input_reported_not_faulted(plan, what):
+    A = gen.erdos_renyi(100, 5, seed=1)
+    B = gen.erdos_renyi(100, 5, seed=2)
+    if what == "a_col":
+        A.col = A.col.copy()
+        A.col[7] = 100          # == B.rows: out of range
+    elif what == "b_col":
+        B.col = B.col.copy()
+        B.col[3] = 1000         # >= B.cols
+    else:
+        A.row_ptr = A.row_ptr.copy()
+        A.row_ptr[50] = A.row_ptr[49] - 1
+    dA, dB = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
+    with pytest.raises(SpgemmError) as e:
+        plan.spgemm(dA, dB)
+    assert e.value.code == _lib.ERR_INVALID
+    # the context is still usable afterwards
+    torch.cuda.synchronize()
+    C = plan.spgemm(DeviceCSR.from_host(gen.erdos_renyi(50, 3, seed=9)),
+                    DeviceCSR.from_host(gen.erdos_renyi(50, 3, seed=9)))
+    assert C.nnz > 0
