@@ -95,6 +95,10 @@ int spgemm_plan_destroy(spgemm_plan* plan);
 int spgemm_workspace_bytes(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
                            size_t* bytes);
 
+/* Zero the workspace's control block (status word, counters). Call once on
+ * a newly allocated workspace before its first use; enqueued on `stream`. */
+int spgemm_workspace_init(const spgemm_plan* plan, void* ws, size_t ws_bytes, void* stream);
+
 /* Intermediate-product counting (Algorithm 1).
  * ip_row   [out, device, A.rows int64]: IP_i = sum over stored (i,k) of |row k of B|.
  * ip_total [out, host, nullable]: sum of ip_row; when non-NULL the call
@@ -150,7 +154,8 @@ int spgemm_numeric(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_cs
 typedef int (*spgemm_alloc_fn)(void* ctx, int64_t nnz, int32_t** col, float** val);
 
 /* The whole product in one call: count, symbolic, row pointers, alloc,
- * numeric. ip_row and row_nnz are device scratch of A.rows entries each,
+ * numeric (the workspace is initialised first). ip_row and row_nnz are
+ * device scratch of A.rows entries each,
  * row_ptr_C the device output of A.rows+1 entries. Synchronises twice (for
  * the nnz of C and for the final status). *nnz_C receives the nnz of C.
  * Returns SPGEMM_ERR_OVERFLOW (before allocating) when C needs more than
@@ -162,6 +167,19 @@ int spgemm(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, vo
 /* Synchronise `stream`, read and clear the workspace's device status word;
  * *status receives the SPGEMM_ERR_* code it maps to (SPGEMM_OK if clean). */
 int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status);
+
+/* Launch accounting and per-kernel timing (diagnostics; not thread-safe
+ * while enabled). Every kernel launch the library makes is counted in
+ * spgemm_launch_total. With profiling on, each launch is bracketed by a
+ * pair of CUDA events on its stream (up to 8192 launches between reads);
+ * spgemm_profile_read synchronises on them and returns, per kernel id, the
+ * summed device milliseconds and the number of timed launches, then resets
+ * the timing slots. spgemm_kernel_name maps an id to a short name. */
+int spgemm_profile_enable(spgemm_plan* plan, int on);
+int spgemm_profile_read(spgemm_plan* plan, double* ms, int64_t* launches, int n);
+int spgemm_kernel_count(void);
+const char* spgemm_kernel_name(int kid);
+int64_t spgemm_launch_total(const spgemm_plan* plan);
 
 /* Short text for a status code. */
 const char* spgemm_status_string(int status);

@@ -54,6 +54,7 @@ PROTOTYPES = {
     "spgemm_plan_create": (ctypes.c_int, [_P(c_vp), _P(OptsStruct), ctypes.c_int]),
     "spgemm_plan_destroy": (ctypes.c_int, [c_vp]),
     "spgemm_workspace_bytes": (ctypes.c_int, [c_vp, _CSR, _CSR, _P(c_sz)]),
+    "spgemm_workspace_init": (ctypes.c_int, [c_vp, c_vp, c_sz, c_vp]),
     "spgemm_count": (ctypes.c_int, [c_vp, _CSR, _CSR, c_vp, c_sz, c_vp, _P(c_i64), c_vp]),
     "spgemm_group": (ctypes.c_int, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp, c_sz, c_vp, c_vp, c_vp]),
     "spgemm_symbolic": (ctypes.c_int, [c_vp, _CSR, _CSR, c_vp, c_vp, c_sz, c_vp, _P(c_i64), c_vp]),
@@ -64,6 +65,11 @@ PROTOTYPES = {
                               _P(c_i64), c_vp]),
     "spgemm_status": (ctypes.c_int, [c_vp, c_vp, c_vp, _P(ctypes.c_int)]),
     "spgemm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "spgemm_profile_enable": (ctypes.c_int, [c_vp, ctypes.c_int]),
+    "spgemm_profile_read": (ctypes.c_int, [c_vp, _P(ctypes.c_double), _P(c_i64), ctypes.c_int]),
+    "spgemm_kernel_count": (ctypes.c_int, []),
+    "spgemm_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "spgemm_launch_total": (c_i64, [c_vp]),
 }
 
 

@@ -116,11 +116,18 @@ class Plan:
               "spgemm_workspace_bytes")
         return int(n.value)
 
-    def workspace(self, A: DeviceCSR, B: DeviceCSR) -> torch.Tensor:
+    def workspace(self, A: DeviceCSR, B: DeviceCSR, stream=None) -> torch.Tensor:
+        """A 256-byte aligned, initialised workspace for operands of these shapes."""
         nbytes = self.workspace_bytes(A, B)
         ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=A.device)
         off = (-ws.data_ptr()) % 256
-        return ws[off:off + nbytes]
+        ws = ws[off:off + nbytes]
+        self.workspace_init(ws, stream)
+        return ws
+
+    def workspace_init(self, ws: torch.Tensor, stream=None) -> None:
+        check(_lib.lib().spgemm_workspace_init(self.handle, _ptr(ws), ws.numel(), _stream(stream)),
+              "spgemm_workspace_init")
 
     # ------------------------------------------------------------------ phases
     def count(self, A: DeviceCSR, B: DeviceCSR, ws: torch.Tensor, ip_row: torch.Tensor | None = None,
@@ -182,6 +189,23 @@ class Plan:
                                         _ptr(row_ptr_C), _ptr(ws), ws.numel(), _ptr(col_C),
                                         _ptr(val_C), _stream(stream)),
               "spgemm_numeric")
+
+    # --------------------------------------------------------- diagnostics
+    def launches(self) -> int:
+        """Kernel launches this plan has made since creation."""
+        return int(_lib.lib().spgemm_launch_total(self.handle))
+
+    def profile(self, on: bool = True) -> None:
+        check(_lib.lib().spgemm_profile_enable(self.handle, 1 if on else 0), "spgemm_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, timed launches)} since the last read."""
+        L = _lib.lib()
+        n = L.spgemm_kernel_count()
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        check(L.spgemm_profile_read(self.handle, ms, cnt, n), "spgemm_profile_read")
+        return {L.spgemm_kernel_name(k).decode(): (ms[k], int(cnt[k])) for k in range(n) if cnt[k]}
 
     def status(self, ws: torch.Tensor, stream=None) -> int:
         st = ctypes.c_int()

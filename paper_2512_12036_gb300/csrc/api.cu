@@ -54,6 +54,41 @@ void init_occupancy(spgemm_plan* p) {
     occupancy_numeric(p);
 }
 
+const char* const kKernelNames[K_NUM_KERNELS] = {
+    "fill", "check_rpt", "zero_total", "ip_count", "sum", "group_hist", "group_scan",
+    "group_scatter", "scan_part", "scan_top", "scan_final", "reset_flag", "bpanel", "sym_esc",
+    "sym_warp", "sym_block", "sym_dense", "num_esc", "num_warp32", "num_warp64", "num_block32",
+    "num_block64", "num_dense32", "num_dense64"};
+
+void prof_begin(const spgemm_plan* p, int kid, cudaStream_t s) {
+    (void)kid;
+    ProfState* st = p->prof;
+    __atomic_fetch_add(&st->launches, 1ull, __ATOMIC_RELAXED);
+    if (st->on && st->n < st->cap) cudaEventRecord(st->ev[2 * st->n], s);
+}
+
+void prof_end(const spgemm_plan* p, int kid, cudaStream_t s) {
+    ProfState* st = p->prof;
+    if (st->on && st->n < st->cap) {
+        cudaEventRecord(st->ev[2 * st->n + 1], s);
+        st->kid[st->n] = kid;
+        ++st->n;
+    }
+}
+
+static void prof_free(ProfState* st) {
+    if (st->ev) {
+        for (int i = 0; i < 2 * st->cap; ++i) cudaEventDestroy(st->ev[i]);
+        free(st->ev);
+        free(st->kid);
+    }
+    st->ev = nullptr;
+    st->kid = nullptr;
+    st->cap = 0;
+    st->n = 0;
+    st->on = 0;
+}
+
 }  // namespace spg
 
 using namespace spg;
@@ -166,6 +201,7 @@ int spgemm_plan_create(spgemm_plan** out, const spgemm_opts* opts, int device) {
     cudaSetDevice(device);
     spgemm_plan* p = (spgemm_plan*)calloc(1, sizeof(spgemm_plan));
     if (!p) return SPGEMM_ERR_INTERNAL;
+    p->prof = new ProfState();
     p->device = device;
     p->opts = o;
     int v = 0;
@@ -177,6 +213,7 @@ int spgemm_plan_create(spgemm_plan** out, const spgemm_opts* opts, int device) {
     cudaError_t e = cudaGetLastError();
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
+        delete p->prof;
         free(p);
         return SPGEMM_ERR_CUDA;
     }
@@ -185,8 +222,78 @@ int spgemm_plan_create(spgemm_plan** out, const spgemm_opts* opts, int device) {
 }
 
 int spgemm_plan_destroy(spgemm_plan* p) {
+    if (!p) return SPGEMM_OK;
+    prof_free(p->prof);
+    delete p->prof;
     free(p);
     return SPGEMM_OK;
+}
+
+int spgemm_profile_enable(spgemm_plan* plan, int on) {
+    if (!plan) return SPGEMM_ERR_INVALID;
+    ProfState* st = plan->prof;
+    if (!on) {
+        prof_free(st);
+        return SPGEMM_OK;
+    }
+    if (st->cap == 0) {
+        const int cap = 8192;
+        st->ev = (cudaEvent_t*)calloc(2 * cap, sizeof(cudaEvent_t));
+        st->kid = (int*)calloc(cap, sizeof(int));
+        if (!st->ev || !st->kid) {
+            prof_free(st);
+            return SPGEMM_ERR_INTERNAL;
+        }
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(plan->device);
+        for (int i = 0; i < 2 * cap; ++i) {
+            if (cudaEventCreate(&st->ev[i]) != cudaSuccess) {
+                st->cap = i / 2;
+                cudaSetDevice(prev);
+                prof_free(st);
+                return SPGEMM_ERR_CUDA;
+            }
+            st->cap = (i + 1) / 2;
+        }
+        cudaSetDevice(prev);
+        st->cap = cap;
+    }
+    st->n = 0;
+    st->on = 1;
+    return SPGEMM_OK;
+}
+
+int spgemm_profile_read(spgemm_plan* plan, double* ms, int64_t* launches, int n) {
+    if (!plan || n < 0 || (n > 0 && (!ms || !launches))) return SPGEMM_ERR_INVALID;
+    ProfState* st = plan->prof;
+    for (int k = 0; k < n; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (int i = 0; i < st->n; ++i) {
+        if (cudaEventSynchronize(st->ev[2 * i + 1]) != cudaSuccess) return SPGEMM_ERR_CUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, st->ev[2 * i], st->ev[2 * i + 1]) != cudaSuccess)
+            return SPGEMM_ERR_CUDA;
+        const int k = st->kid[i];
+        if (k < n) {
+            ms[k] += t;
+            launches[k] += 1;
+        }
+    }
+    st->n = 0;
+    return SPGEMM_OK;
+}
+
+int spgemm_kernel_count(void) { return K_NUM_KERNELS; }
+
+const char* spgemm_kernel_name(int kid) {
+    return (kid >= 0 && kid < K_NUM_KERNELS) ? kKernelNames[kid] : "unknown";
+}
+
+int64_t spgemm_launch_total(const spgemm_plan* plan) {
+    return plan ? (int64_t)__atomic_load_n(&plan->prof->launches, __ATOMIC_RELAXED) : 0;
 }
 
 int spgemm_workspace_bytes(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
@@ -195,6 +302,12 @@ int spgemm_workspace_bytes(const spgemm_plan* plan, const spgemm_csr* A, const s
     if (A->rows < 0 || B->rows < 0 || B->cols < 0) return SPGEMM_ERR_INVALID;
     *bytes = ws_layout(plan, A->rows, B->rows, B->cols).total;
     return SPGEMM_OK;
+}
+
+int spgemm_workspace_init(const spgemm_plan* plan, void* ws, size_t ws_bytes, void* stream) {
+    if (!plan) return SPGEMM_ERR_INVALID;
+    if (!ws || ws_bytes < sizeof(Ctl) || ((uintptr_t)ws & 255)) return SPGEMM_ERR_WORKSPACE;
+    return cuda_err(cudaMemsetAsync(ws, 0, sizeof(Ctl), (cudaStream_t)stream));
 }
 
 int spgemm_count(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, void* ws,
@@ -248,7 +361,7 @@ int spgemm_symbolic(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_c
     CsrDev dA = dev_view(A), dB = dev_view(B);
     launch_symbolic(plan, dA, dB, (const long long*)ip_row, w, row_nnz, s);
     launch_bpanel(plan, dB, w, s);
-    launch_nnz_total(row_nnz, A->rows, w, s);
+    launch_nnz_total(plan, row_nnz, A->rows, w, s);
     rc = cuda_err(cudaGetLastError());
     if (rc) return rc;
     if (nnz_total) return sync_read(w.ctl, 1, nnz_total, s);
@@ -293,6 +406,8 @@ int spgemm(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, vo
     int rc = check_pair(plan, A, B, true);
     if (rc) return rc;
     if (!alloc || !nnz_C || !row_ptr_C) return SPGEMM_ERR_INVALID;
+    rc = spgemm_workspace_init(plan, ws, ws_bytes, stream);
+    if (rc) return rc;
     rc = spgemm_count(plan, A, B, ws, ws_bytes, ip_row, nullptr, stream);
     if (rc) return rc;
     int64_t total = 0;

@@ -14,11 +14,11 @@ __global__ void k_fill_i64(long long* p, long long n, long long v) {
         p[i] = v;
 }
 
-void launch_fill_i64(long long* p, long long n, long long v, cudaStream_t s) {
+void launch_fill_i64(const spgemm_plan* pl, long long* p, long long n, long long v, cudaStream_t s) {
     if (n <= 0) return;
     long long blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    k_fill_i64<<<(int)blocks, 256, 0, s>>>(p, n, v);
+    SPG_LAUNCH(pl, K_FILL, s, k_fill_i64<<<(int)blocks, 256, 0, s>>>(p, n, v));
 }
 
 template <typename T>
@@ -109,28 +109,27 @@ __global__ void __launch_bounds__(kCountThreads) k_ip_count(CsrDev A, CsrDev B, 
 
 void launch_ip_count(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, long long* ip,
                      const WsPtrs& w, cudaStream_t s) {
-    (void)p;
     if (A.rows == 0) return;
-    launch_fill_i64(ip, A.rows, 0, s);
+    launch_fill_i64(p, ip, A.rows, 0, s);
     {
         const int blocks = (int)((A.rows + 255) / 256 < 4096 ? (A.rows + 255) / 256 : 4096);
-        k_check_rpt<<<blocks, 256, 0, s>>>(A, w.ctl);
+        SPG_LAUNCH(p, K_CHECK_RPT, s, k_check_rpt<<<blocks, 256, 0, s>>>(A, w.ctl));
     }
     if (B.rows > 0) {
         const int blocks = (int)((B.rows + 255) / 256 < 4096 ? (B.rows + 255) / 256 : 4096);
-        k_check_rpt<<<blocks, 256, 0, s>>>(B, w.ctl);
+        SPG_LAUNCH(p, K_CHECK_RPT, s, k_check_rpt<<<blocks, 256, 0, s>>>(B, w.ctl));
     }
-    k_zero_total<<<1, 1, 0, s>>>(w.ctl, 0);
+    SPG_LAUNCH(p, K_ZERO, s, k_zero_total<<<1, 1, 0, s>>>(w.ctl, 0));
     if (A.nnz > 0) {
         const long long tiles = (A.nnz + kCountTile - 1) / kCountTile;
-        k_ip_count<<<(unsigned)tiles, kCountThreads, 0, s>>>(A, B, ip, w.ctl);
+        SPG_LAUNCH(p, K_IP_COUNT, s, k_ip_count<<<(unsigned)tiles, kCountThreads, 0, s>>>(A, B, ip, w.ctl));
     }
-    k_sum_to<long long><<<256, 256, 0, s>>>(ip, A.rows, &w.ctl->totals[0]);
+    SPG_LAUNCH(p, K_SUM, s, k_sum_to<long long><<<256, 256, 0, s>>>(ip, A.rows, &w.ctl->totals[0]));
 }
 
-void launch_nnz_total(const int* row_nnz, int n, const WsPtrs& w, cudaStream_t s) {
-    k_zero_total<<<1, 1, 0, s>>>(w.ctl, 1);
-    if (n > 0) k_sum_to<int><<<256, 256, 0, s>>>(row_nnz, n, &w.ctl->totals[1]);
+void launch_nnz_total(const spgemm_plan* p, const int* row_nnz, int n, const WsPtrs& w, cudaStream_t s) {
+    SPG_LAUNCH(p, K_ZERO, s, k_zero_total<<<1, 1, 0, s>>>(w.ctl, 1));
+    if (n > 0) SPG_LAUNCH(p, K_SUM, s, k_sum_to<int><<<256, 256, 0, s>>>(row_nnz, n, &w.ctl->totals[1]));
 }
 
 // ---------------------------------------------------------------------------
@@ -243,12 +242,15 @@ __global__ void __launch_bounds__(kBinRows) k_group_scatter(GroupArgs g, int nbl
 
 void launch_group(const spgemm_plan* p, const GroupArgs& g, const WsPtrs& w, int* map_out,
                   int* offsets_out, cudaStream_t s) {
-    (void)p;
     const int nblk = (g.n + kBinRows - 1) / kBinRows;
-    if (nblk > 0) k_group_hist<<<nblk, kBinRows, 0, s>>>(g, nblk, w.blk_counts);
-    k_group_scan<<<1, 1024, 0, s>>>(nblk, w.blk_counts, w.ctl, offsets_out,
-                                    g.phase == 2 ? g.nthr + 1 : 0);
-    if (nblk > 0) k_group_scatter<<<nblk, kBinRows, 0, s>>>(g, nblk, w.blk_counts, map_out);
+    if (nblk > 0)
+        SPG_LAUNCH(p, K_GROUP_HIST, s, k_group_hist<<<nblk, kBinRows, 0, s>>>(g, nblk, w.blk_counts));
+    SPG_LAUNCH(p, K_GROUP_SCAN, s,
+               k_group_scan<<<1, 1024, 0, s>>>(nblk, w.blk_counts, w.ctl, offsets_out,
+                                               g.phase == 2 ? g.nthr + 1 : 0));
+    if (nblk > 0)
+        SPG_LAUNCH(p, K_GROUP_SCATTER, s,
+                   k_group_scatter<<<nblk, kBinRows, 0, s>>>(g, nblk, w.blk_counts, map_out));
 }
 
 // ---------------------------------------------------------------------------
@@ -331,11 +333,14 @@ __global__ void __launch_bounds__(1024) k_scan_final(const int* x, int n, const 
 
 void launch_row_ptr(const spgemm_plan* p, const int* row_nnz, int n, const WsPtrs& w,
                     int* row_ptr, cudaStream_t s) {
-    (void)p;
     const int nscan = (n + kScanItems - 1) / kScanItems;
-    if (nscan > 0) k_scan_part<<<nscan, 1024, 0, s>>>(row_nnz, n, w.scan_part);
-    k_scan_top<<<1, 1024, 0, s>>>(w.scan_part, nscan, w.ctl, row_ptr, n);
-    if (nscan > 0) k_scan_final<<<nscan, 1024, 0, s>>>(row_nnz, n, w.scan_part, row_ptr);
+    if (nscan > 0)
+        SPG_LAUNCH(p, K_SCAN_PART, s, k_scan_part<<<nscan, 1024, 0, s>>>(row_nnz, n, w.scan_part));
+    SPG_LAUNCH(p, K_SCAN_TOP, s,
+               k_scan_top<<<1, 1024, 0, s>>>(w.scan_part, nscan, w.ctl, row_ptr, n));
+    if (nscan > 0)
+        SPG_LAUNCH(p, K_SCAN_FINAL, s,
+                   k_scan_final<<<nscan, 1024, 0, s>>>(row_nnz, n, w.scan_part, row_ptr));
 }
 
 }  // namespace spg

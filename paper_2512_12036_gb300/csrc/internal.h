@@ -8,7 +8,28 @@
 #include "../../include/spgemm.h"
 #include "common.cuh"
 
+namespace spg {
+// Kernel ids for launch counting and per-kernel CUDA-event timing.
+enum KernelId : int {
+    K_FILL, K_CHECK_RPT, K_ZERO, K_IP_COUNT, K_SUM, K_GROUP_HIST, K_GROUP_SCAN, K_GROUP_SCATTER,
+    K_SCAN_PART, K_SCAN_TOP, K_SCAN_FINAL, K_RESET, K_BPANEL, K_SYM_ESC, K_SYM_WARP, K_SYM_BLOCK,
+    K_SYM_DENSE, K_NUM_ESC, K_NUM_WARP32, K_NUM_WARP64, K_NUM_BLOCK32, K_NUM_BLOCK64,
+    K_NUM_DENSE32, K_NUM_DENSE64, K_NUM_KERNELS
+};
+extern const char* const kKernelNames[K_NUM_KERNELS];
+
+struct ProfState {
+    int on = 0;
+    int n = 0;
+    int cap = 0;
+    int* kid = nullptr;
+    cudaEvent_t* ev = nullptr;
+    unsigned long long launches = 0;        // all launches since plan creation
+};
+}  // namespace spg
+
 struct spgemm_plan {
+    spg::ProfState* prof;
     int device;
     int num_sms;
     size_t smem_optin;     // max dynamic shared memory per block
@@ -71,7 +92,7 @@ struct WsPtrs {
 WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols);
 
 // Launchers (stream-ordered, no host synchronisation).
-void launch_fill_i64(long long* p, long long n, long long v, cudaStream_t s);
+void launch_fill_i64(const spgemm_plan* pl, long long* p, long long n, long long v, cudaStream_t s);
 void launch_ip_count(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, long long* ip,
                      const WsPtrs& w, cudaStream_t s);
 
@@ -96,12 +117,23 @@ void launch_row_ptr(const spgemm_plan* p, const int* row_nnz, int n, const WsPtr
 
 void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
                      const WsPtrs& w, int* row_nnz, cudaStream_t s);
-void launch_nnz_total(const int* row_nnz, int n, const WsPtrs& w, cudaStream_t s);
+void launch_nnz_total(const spgemm_plan* p, const int* row_nnz, int n, const WsPtrs& w, cudaStream_t s);
 
 void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
                     int row_begin, int row_end, const int* rptC, const WsPtrs& w, int* colC,
                     float* valC, cudaStream_t s);
 
 void init_occupancy(spgemm_plan* p);
+
+void prof_begin(const spgemm_plan* p, int kid, cudaStream_t s);
+void prof_end(const spgemm_plan* p, int kid, cudaStream_t s);
+
+// Launch a kernel with launch counting and (when enabled) event timing.
+#define SPG_LAUNCH(plan, kid, stream, ...)            \
+    do {                                              \
+        ::spg::prof_begin((plan), (kid), (stream));   \
+        __VA_ARGS__;                                  \
+        ::spg::prof_end((plan), (kid), (stream));     \
+    } while (0)
 
 }  // namespace spg

@@ -458,12 +458,12 @@ void occupancy_numeric(spgemm_plan* p) {
 __global__ void k_reset_bflag(Ctl* ctl) { ctl->b_unsorted = 0; }
 
 void launch_bpanel(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaStream_t s) {
-    k_reset_bflag<<<1, 1, 0, s>>>(w.ctl);
+    SPG_LAUNCH(p, K_RESET, s, k_reset_bflag<<<1, 1, 0, s>>>(w.ctl));
     if (w.bpanel == nullptr || B.rows == 0) return;
     const long long warps = B.rows;
     long long blocks = (warps * 32 + 255) / 256;
     if (blocks > (long long)p->num_sms * 16) blocks = (long long)p->num_sms * 16;
-    k_bpanel<<<(int)blocks, 256, 0, s>>>(B, w.panels, w.panel_cols, w.bpanel, w.ctl);
+    SPG_LAUNCH(p, K_BPANEL, s, k_bpanel<<<(int)blocks, 256, 0, s>>>(B, w.panels, w.panel_cols, w.bpanel, w.ctl));
 }
 
 void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
@@ -480,25 +480,31 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     launch_group(p, g, w, w.map, nullptr, s);
     if (g.n == 0) return;
     const int sms = p->num_sms;
-    k_num_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_ESC);
-    k_num_warp<float><<<sms * p->occ_num_warp32, kWarpsPerBlockNW * 32, num_warp_smem(4), s>>>(
-        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP32);
-    k_num_warp<double><<<sms * p->occ_num_warp64, kWarpsPerBlockNW * 32, num_warp_smem(8), s>>>(
-        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP64);
+    SPG_LAUNCH(p, K_NUM_ESC, s, k_num_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_ESC));
+    SPG_LAUNCH(p, K_NUM_WARP32, s,
+               k_num_warp<float><<<sms * p->occ_num_warp32, kWarpsPerBlockNW * 32, num_warp_smem(4), s>>>(
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP32));
+    SPG_LAUNCH(p, K_NUM_WARP64, s,
+               k_num_warp<double><<<sms * p->occ_num_warp64, kWarpsPerBlockNW * 32, num_warp_smem(8), s>>>(
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP64));
     const unsigned tb = pow2_ceil(2u * (unsigned)p->opts.block_max_nnz);
     int max_bits = 0;
     while ((1u << max_bits) < tb) ++max_bits;
-    k_num_block<float><<<sms * p->occ_num_block32, kNumBlockThreads, num_block_smem(p, 4), s>>>(
-        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK32, 2, max_bits);
-    k_num_block<double><<<sms * p->occ_num_block64, kNumBlockThreads, num_block_smem(p, 8), s>>>(
-        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits);
+    SPG_LAUNCH(p, K_NUM_BLOCK32, s,
+               k_num_block<float><<<sms * p->occ_num_block32, kNumBlockThreads, num_block_smem(p, 4), s>>>(
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK32, 2, max_bits));
+    SPG_LAUNCH(p, K_NUM_BLOCK64, s,
+               k_num_block<double><<<sms * p->occ_num_block64, kNumBlockThreads, num_block_smem(p, 8), s>>>(
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits));
     const int PW = w.panel_cols;
-    k_num_dense<float><<<sms * p->occ_num_dense32, kNumDenseThreads, num_dense_smem(p, 4), s>>>(
-        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0, NB_DENSE32_0 + NB_DENSE_N,
-        4, w.bpanel, w.panels, PW);
-    k_num_dense<double><<<sms * p->occ_num_dense64, kNumDenseThreads, num_dense_smem(p, 8), s>>>(
-        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0, NB_DENSE64_0 + NB_DENSE_N,
-        5, w.bpanel, w.panels, PW);
+    SPG_LAUNCH(p, K_NUM_DENSE32, s,
+               k_num_dense<float><<<sms * p->occ_num_dense32, kNumDenseThreads, num_dense_smem(p, 4), s>>>(
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
+                   NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW));
+    SPG_LAUNCH(p, K_NUM_DENSE64, s,
+               k_num_dense<double><<<sms * p->occ_num_dense64, kNumDenseThreads, num_dense_smem(p, 8), s>>>(
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
+                   NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW));
 }
 
 }  // namespace spg

@@ -230,18 +230,21 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     launch_group(p, g, w, w.map, nullptr, s);
     if (A.rows == 0) return;
     const int sms = p->num_sms;
-    k_sym_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, row_nnz, SB_ESC);
+    SPG_LAUNCH(p, K_SYM_ESC, s, k_sym_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, row_nnz, SB_ESC));
     const size_t sw = (size_t)kWarpsPerBlockSW * kWarpTableSym * 4;
-    k_sym_warp<<<sms * p->occ_sym_warp, kWarpsPerBlockSW * 32, sw, s>>>(A, B, ip, w.map, w.ctl,
-                                                                       row_nnz, SB_WARP);
+    SPG_LAUNCH(p, K_SYM_WARP, s,
+               k_sym_warp<<<sms * p->occ_sym_warp, kWarpsPerBlockSW * 32, sw, s>>>(
+                   A, B, ip, w.map, w.ctl, row_nnz, SB_WARP));
     const unsigned tb = pow2_ceil(2u * (unsigned)p->opts.block_max_ip);
     int max_bits = 0;
     while ((1u << max_bits) < tb) ++max_bits;
-    k_sym_block<<<sms * p->occ_sym_block, kSymBlockThreads, (size_t)tb * 4, s>>>(
-        A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, SB_BLOCK0 + SB_BLOCK_N, 0, max_bits);
+    SPG_LAUNCH(p, K_SYM_BLOCK, s,
+               k_sym_block<<<sms * p->occ_sym_block, kSymBlockThreads, (size_t)tb * 4, s>>>(
+                   A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, SB_BLOCK0 + SB_BLOCK_N, 0, max_bits));
     const size_t sd = sym_dense_smem(p);
-    k_sym_dense<<<sms * p->occ_sym_dense, kSymDenseThreads, sd, s>>>(
-        A, B, w.map, w.ctl, row_nnz, SB_DENSE0, SB_DENSE0 + SB_DENSE_N, 1, (int)(sd / 4));
+    SPG_LAUNCH(p, K_SYM_DENSE, s,
+               k_sym_dense<<<sms * p->occ_sym_dense, kSymDenseThreads, sd, s>>>(
+                   A, B, w.map, w.ctl, row_nnz, SB_DENSE0, SB_DENSE0 + SB_DENSE_N, 1, (int)(sd / 4)));
 }
 
 }  // namespace spg
