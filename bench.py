@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""SpGEMM throughput benchmark on one GB300 (or N replicas under torchrun).
+
+Workload (one step = the whole hot path over one synthetic input):
+  A = R-MAT scale 20, edge factor 16, (a,b,c,d) = (0.57,0.19,0.19,0.05),
+      symmetrised, deduplicated, no self-loops, fp32 U(0,1] (seed 2);
+  1. C = A*A, produced in blocks of consecutive rows with int32 row pointers
+     (nnz(C) ~ 2.2e10 > 2^31-1): count, allocation phase, per-block row
+     pointers and accumulation phase;
+  2. graph contraction S^T * A * S with S a 2^20 x 65,536 assignment matrix
+     (one 1.0 per row at a uniform cluster id, seed 3): two more products.
+The metric is GFLOP/s = 2 * (intermediate products of the three products) /
+step time. Inputs are resident in HBM before timing; they are larger than
+L2 (A alone is 250 MB vs 129 MB of L2), so no flush is needed between steps.
+
+`--impl reference` times the CPU oracle (plain C, fp64 dense accumulator) on
+the host cores over a bounded sample of rows of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spgemm_gflops"
+UNIT = "GFLOP/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(scale: int):
+    from paper_2512_12036_gb300 import gen
+    A = gen.rmat_symmetric(scale, 16, 0.57, 0.19, 0.19, seed=2)
+    clusters = max(1, (1 << scale) // 16)
+    S = gen.assignment_matrix(A.rows, clusters, seed=3)
+    St = gen.transpose_structure(S)
+    return A, S, St, clusters
+
+
+def workload_name(scale: int) -> str:
+    return f"rmat{scale}_ef16_AxA_plus_StAS"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (rank 0 only): a bounded random sample of rows of A*A.
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(A, seconds: float, seed: int = 0):
+    import oracle
+    rng = np.random.default_rng(seed)
+    ip, _ = oracle.ip_count(A, A)
+    cores = oracle.max_threads()
+    # calibrate on a small sample, then size the main one to ~`seconds`
+    order = rng.permutation(A.rows).astype(np.int32)
+    csum = np.cumsum(ip[order])
+
+    def take(products):
+        k = int(np.searchsorted(csum, products)) + 1
+        return order[:min(k, order.size)]
+
+    cal = take(2e7)
+    t0 = time.perf_counter()
+    oracle.spgemm(A, A, rows=cal, with_bound=False)
+    t_cal = max(time.perf_counter() - t0, 1e-3)
+    rate = float(ip[cal].sum()) / t_cal
+    rows = take(rate * seconds)
+    prods = float(ip[rows].sum())
+    t0 = time.perf_counter()
+    oracle.spgemm(A, A, rows=rows, with_bound=False)
+    t = time.perf_counter() - t0
+    return {"value": 2 * prods / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{rows.size} uniformly drawn rows of A*A ({prods:.3e} intermediate "
+                      f"products, {t:.1f} s), fp64 dense accumulator, OpenMP over rows"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+
+def tier_work(plan, A_host, ip, nnz):
+    """Rows, products and compulsory bytes of each row tier of the allocation
+    and accumulation phases of A*A, following the library's tier rules (used
+    for the per-kernel roofline)."""
+    o = plan.opts
+    na = np.diff(A_host.row_ptr.astype(np.int64))
+    small = (ip <= o["esc_max"]) & (na <= o["esc_max"])
+    # allocation phase: tiers by IP
+    live = ip > 1
+    s_esc = live & small
+    s_warp = live & ~small & (ip <= o["warp_max_ip"])
+    s_block = live & ~small & ~s_warp & (ip <= o["block_max_ip"])
+    s_dense = live & ~small & ~s_warp & ~s_block
+    # accumulation phase: tiers by nnz, fp64 where > fp32_max_terms terms can meet
+    f64 = (na > o["fp32_max_terms"]) & (ip > o["fp32_max_terms"])
+    has = nnz > 0
+    n_esc = has & small
+    n_warp = has & ~small & (nnz <= o["warp_max_nnz"]) & (ip <= 16 * o["warp_max_nnz"])
+    n_block = has & ~small & ~n_warp & (nnz <= o["block_max_nnz"])
+    n_dense = has & ~small & ~n_warp & ~n_block
+    tiers = {"sym_esc": (s_esc, 0), "sym_warp": (s_warp, 0), "sym_block": (s_block, 0),
+             "sym_dense": (s_dense, 0),
+             "num_esc": (n_esc, 1), "num_warp32": (n_warp & ~f64, 1), "num_warp64": (n_warp & f64, 1),
+             "num_block32": (n_block & ~f64, 1), "num_block64": (n_block & f64, 1),
+             "num_dense32": (n_dense & ~f64, 1), "num_dense64": (n_dense & f64, 1)}
+    out = {}
+    for k, (m, numeric) in tiers.items():
+        rows, prods, ents, cn = int(m.sum()), int(ip[m].sum()), int(na[m].sum()), int(nnz[m].sum())
+        if numeric:
+            # A rows (row_ptr pair, col+val), gathered B row_ptr pairs, B col+val per
+            # product, C col+val per entry
+            byts = 8 * rows + 8 * ents + 8 * ents + 8 * prods + 8 * cn
+        else:
+            # A rows (row_ptr pair, col), gathered B row_ptr pairs, B col per product,
+            # one count per row
+            byts = 8 * rows + 4 * ents + 8 * ents + 4 * prods + 4 * rows
+        out[k] = {"rows": rows, "ip": prods, "a_entries": ents, "nnz": cn, "bytes": byts}
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2512_12036_gb300 import DeviceCSR, Plan
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    A_h, S_h, St_h, clusters = workload(args.scale)
+    dev = torch.device("cuda", local)
+    A = DeviceCSR.from_host(A_h, dev)
+    S = DeviceCSR.from_host(S_h, dev)
+    St = DeviceCSR.from_host(St_h, dev)
+    plan = Plan(device=local)
+    ws_aa = plan.workspace(A, A)
+    ws_sa = plan.workspace(St, A)
+
+    # first pass: sizes and output buffers (untimed)
+    blocks, ip_aa, nnz_aa = plan.spgemm_blocks(A, A, ws=ws_aa)
+    T_blocks, ip_sa, _ = plan.spgemm_blocks(St, A, ws=ws_sa)
+    T = T_blocks[0][2]
+    ws_ts = plan.workspace(T, S)
+    C2_blocks, ip_ts, nnz_ts = plan.spgemm_blocks(T, S, ws=ws_ts)
+    for ws in (ws_aa, ws_sa, ws_ts):
+        plan.check_status(ws, "first pass")
+    ip_step = ip_aa + ip_sa + ip_ts
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.spgemm_blocks(A, A, ws=ws_aa, out=blocks)
+        plan.spgemm_blocks(St, A, ws=ws_sa, out=T_blocks)
+        plan.spgemm_blocks(T, S, ws=ws_ts, out=C2_blocks)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for ws in (ws_aa, ws_sa, ws_ts):
+        plan.check_status(ws, "warm-up")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs)
+    plan.profile(True)
+    launches0 = plan.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = plan.launches() - launches0
+    prof = plan.profile_read()
+    plan.profile(False)
+    for ws in (ws_aa, ws_sa, ws_ts):
+        plan.check_status(ws, "timed steps")
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = 2.0 * ip_step * world / (ms_step / 1e3) / 1e9
+
+    # ---- per-kernel roofline for the dominant kernel
+    ip_row = torch.empty(A.rows, dtype=torch.int64, device=dev)
+    ip_row, _ = plan.count(A, A, ws_aa, ip_row=ip_row)
+    nnz_row, _ = plan.symbolic(A, A, ip_row, ws_aa)
+    work = tier_work(plan, A_h, ip_row.cpu().numpy(), nnz_row.to(torch.int64).cpu().numpy())
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    top_name, (top_ms, top_n) = top
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    roof = None
+    if top_name in work and top_ms > 0:
+        # algorithmic bytes the kernel moves per step (its tier's rows of A*A) over
+        # its measured device time per step (= bytes per launch / mean launch time)
+        bytes_step = work[top_name]["bytes"]
+        achieved = bytes_step / (top_ms / args.steps / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak_gbs,
+                "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "launches_per_step": top_n / args.steps,
+                "bytes_per_step": int(bytes_step),
+                "share_of_step": top_ms / ms}
+    compulsory = (4 * (A.rows + 1) + 8 * A.nnz) + (8 * ip_aa + 8 * A.nnz) + (8 * nnz_aa + 4 * (A.rows + 1))
+    step_frac = compulsory / (ms_step / 1e3) / (peak_gbs * 1e9)
+
+    # ---- end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+               {"rp": A_h.row_ptr, "col": A_h.col, "val": A_h.val, "srp": S_h.row_ptr,
+                "scol": S_h.col, "sval": S_h.val, "trp": St_h.row_ptr, "tcol": St_h.col,
+                "tval": St_h.val}.items()}
+        h2d = sum(t.numel() * t.element_size() for t in pin.values())
+        host_rp = [torch.empty(b[2].row_ptr.numel(), dtype=torch.int32).pin_memory() for b in blocks]
+        host_c2 = [torch.empty(C2_blocks[0][2].row_ptr.numel(), dtype=torch.int32).pin_memory(),
+                   torch.empty(C2_blocks[0][2].nnz, dtype=torch.int32).pin_memory(),
+                   torch.empty(C2_blocks[0][2].nnz, dtype=torch.float32).pin_memory()]
+        d2h = sum(t.numel() * t.element_size() for t in host_rp + host_c2)
+
+        def e2e_step():
+            A.row_ptr.copy_(pin["rp"], non_blocking=True)
+            A.col.copy_(pin["col"], non_blocking=True)
+            A.val.copy_(pin["val"], non_blocking=True)
+            S.row_ptr.copy_(pin["srp"], non_blocking=True)
+            S.col.copy_(pin["scol"], non_blocking=True)
+            S.val.copy_(pin["sval"], non_blocking=True)
+            St.row_ptr.copy_(pin["trp"], non_blocking=True)
+            St.col.copy_(pin["tcol"], non_blocking=True)
+            St.val.copy_(pin["tval"], non_blocking=True)
+            step()
+            for hb, (_, _, Cb) in zip(host_rp, blocks):
+                hb.copy_(Cb.row_ptr, non_blocking=True)
+            C2 = C2_blocks[0][2]
+            host_c2[0].copy_(C2.row_ptr, non_blocking=True)
+            host_c2[1].copy_(C2.col, non_blocking=True)
+            host_c2[2].copy_(C2.val, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": 2.0 * ip_step * world / (ems / args.steps / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "note": "inputs copied from pinned host memory each step; C(S^T A S) and the "
+                       "row pointers of every A*A block read back (the A*A values stay in HBM)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(A_h, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (fp64 accumulation where "
+            "more than 167 terms can meet)", "data": "synthetic",
+            "config": {"workload": workload_name(args.scale), "rmat_scale": args.scale,
+                       "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05],
+                       "nnz_A": A.nnz, "clusters": clusters, "ip_step": ip_step,
+                       "ip_AxA": ip_aa, "nnz_AxA": nnz_aa, "row_blocks_AxA": len(blocks),
+                       "nnz_StAS": nnz_ts, "l2": "inputs larger than L2, no flush",
+                       "parallelism": f"replicas{world}"},
+            "roofline": roof,
+            "step_hbm_fraction": {"compulsory_bytes_AxA": int(compulsory), "frac": step_frac,
+                                  "peak_gbs": peak_gbs},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "kernel_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in
+                                   sorted(prof.items(), key=lambda kv: -kv[1][0])},
+            "tiers_AxA": {k: {q: v[q] for q in ("rows", "ip", "nnz")} for k, v in work.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    A_h, _, _, _ = workload(args.scale)
+    ip, _ = oracle.ip_count(A_h, A_h)
+    cores = oracle.max_threads()
+    rng = np.random.default_rng(1)
+    # each step: a fresh uniformly drawn sample of ~1e8 intermediate products
+    target = 1e8 if args.scale >= 18 else 1e7
+    samples = []
+    for _ in range(args.warmup + args.steps):
+        order = rng.permutation(A_h.rows).astype(np.int32)
+        k = int(np.searchsorted(np.cumsum(ip[order]), target)) + 1
+        samples.append(order[:k])
+    for r in samples[:args.warmup]:
+        oracle.spgemm(A_h, A_h, rows=r, with_bound=False)
+    prods = 0.0
+    t0 = time.perf_counter()
+    for r in samples[args.warmup:]:
+        oracle.spgemm(A_h, A_h, rows=r, with_bound=False)
+        prods += float(ip[r].sum())
+    t = time.perf_counter() - t0
+    value = 2 * prods / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.scale), "rmat_scale": args.scale},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step ~{target:.0e} intermediate products of A*A "
+                                       "from uniformly drawn rows"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

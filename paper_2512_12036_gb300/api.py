@@ -253,7 +253,7 @@ class Plan:
         from an earlier call with the same operands."""
         if ws is None:
             ws = self.workspace(A, B)
-        ip_row, ip_total = self.count(A, B, ws, stream=stream)
+        ip_row, ip_total = self.count(A, B, ws, total=out is None, stream=stream)
         row_nnz, nnz_total = self.symbolic(A, B, ip_row, ws, stream=stream)
         bounds = split_rows(row_nnz, max_block_nnz)
         blocks = []

@@ -190,7 +190,7 @@ int spgemm_plan_create(spgemm_plan** out, const spgemm_opts* opts, int device) {
     if (o.block_max_ip < o.warp_max_ip || o.block_max_ip > 32768) return SPGEMM_ERR_INVALID;
     if (o.warp_max_nnz < 1 || o.warp_max_nnz > kWarpTableNum / 2) return SPGEMM_ERR_INVALID;
     if (o.block_max_nnz < o.warp_max_nnz || o.block_max_nnz > 8192) return SPGEMM_ERR_INVALID;
-    if (o.panel_cols < 1024 || o.panel_cols > 32 * kNumDenseThreads || (o.panel_cols & 31))
+    if (o.panel_cols < 1024 || o.panel_cols > 16384 || (o.panel_cols & 1023))
         return SPGEMM_ERR_INVALID;
     if (o.fp32_max_terms < 0) return SPGEMM_ERR_INVALID;
     int ndev = 0;

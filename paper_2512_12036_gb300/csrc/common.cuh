@@ -230,4 +230,166 @@ __device__ __forceinline__ void warp_expand(const CsrDev& A, const CsrDev& B, in
     }
 }
 
+
+// Block-wide exclusive scan of one 64-bit value per thread (scratch: 33 slots).
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long v,
+                                                                  unsigned long long* scratch,
+                                                                  unsigned long long* total) {
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long n = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) scratch[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long wv = lane < nwarps ? scratch[lane] : 0ull;
+        unsigned long long wi = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long n = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += n;
+        }
+        scratch[lane] = wi - wv;
+        if (lane == 31) scratch[32] = wi;
+    }
+    __syncthreads();
+    const unsigned long long r = scratch[warp] + incl - v;
+    *total = scratch[32];
+    __syncthreads();
+    return r;
+}
+
+// Shared-memory staging for block_expand: one tile of kT A entries.
+template <int kT, typename Acc>
+struct ExpandTile {
+    long long off[kT + 1];        // exclusive prefix of segment lengths (non-empty entries)
+    int bs[kT];                   // segment start in B
+    Acc a[kT];                    // a_ik (accumulation phase only)
+    unsigned long long scratch[33];
+};
+
+// Block-wide, load-balanced expansion of the products of one tile of A
+// entries. Every thread of the block calls it with the B segment
+// [bs, bs+len) and multiplier a of its own entry (len = 0: none). Empty
+// segments are compacted away by a block scan and an exclusive prefix of
+// the lengths is kept in shared memory. The tile's products are then cut
+// into equal, 32-aligned ranges, one per warp, so every warp does the same
+// work whatever the B-row lengths. A warp walks its range 32 products at a
+// time: when the 32 fall inside one segment (the common case for long B
+// rows) lane l simply takes position bs + offset + l; otherwise lanes find
+// their segment in a 32-entry window of the prefix (segments are non-empty,
+// so 32 products never span more than 32 of them). Loads coalesce along
+// each segment. Products are handled kUnroll steps at a time: load(t) for
+// all of them first (independent loads in flight), then apply(item, a) in
+// order. Ends with a block barrier.
+template <int kT, typename Acc, int kUnroll, class Load, class Apply>
+__device__ __forceinline__ void expand_tile(ExpandTile<kT, Acc>& sm, int bs, int len, Acc a,
+                                            Load&& load, Apply&& apply) {
+    using Item = decltype(load(0));
+    const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    constexpr int kWarps = kT / 32;
+    constexpr unsigned long long kMask48 = (1ull << 48) - 1ull;
+    const unsigned long long v = len > 0 ? ((1ull << 48) | (unsigned long long)len) : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_excl_scan_u64(v, sm.scratch, &tot);
+    if (len > 0) {
+        const int ci = (int)(ex >> 48);
+        sm.off[ci] = (long long)(ex & kMask48);
+        sm.bs[ci] = bs;
+        sm.a[ci] = a;
+    }
+    const int nE = (int)(tot >> 48);
+    const long long P = (long long)(tot & kMask48);
+    if (tid == 0) sm.off[nE] = P;
+    __syncthreads();
+    const long long per = ((P + 32ll * kWarps - 1) / (32ll * kWarps)) * 32ll;
+    long long base = (long long)warp * per;
+    const long long wend = base + per < P ? base + per : P;
+    if (base < wend) {
+        // segment holding product `base`: largest e with off[e] <= base
+        int lo = 0, hi = nE - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sm.off[mid] <= base) lo = mid;
+            else hi = mid - 1;
+        }
+        int s = lo;
+        long long so = sm.off[s], se = sm.off[s + 1];
+        int sbs = sm.bs[s];
+        Acc sa = sm.a[s];
+        while (base < wend) {
+            int tq[kUnroll];
+            Acc aq[kUnroll];
+            bool vq[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                vq[u] = false;
+                tq[u] = 0;
+                aq[u] = Acc(0);
+                if (base < wend) {                       // warp-uniform
+                    if (base + 32 <= se) {               // the 32 products lie in segment s
+                        tq[u] = sbs + (int)(base - so) + lane;
+                        aq[u] = sa;
+                        vq[u] = base + lane < wend;
+                        base += 32;
+                        if (base == se && s + 1 < nE) {
+                            ++s;
+                            so = se;
+                            se = sm.off[s + 1];
+                            sbs = sm.bs[s];
+                            sa = sm.a[s];
+                        }
+                    } else {
+                        const int e = s + lane;
+                        long long d = e <= nE ? sm.off[e] - base : (1ll << 30);
+                        if (d > (1ll << 30)) d = 1ll << 30;
+                        const int rel = (int)d;      // lane 0: <= 0, then non-decreasing
+                        const int wbs = e < nE ? sm.bs[e] : 0;
+                        const Acc wa = e < nE ? sm.a[e] : Acc(0);
+                        const int src = warp_find_src(rel, lane);
+                        tq[u] = __shfl_sync(kFull, wbs, src) + (lane - __shfl_sync(kFull, rel, src));
+                        aq[u] = __shfl_sync(kFull, wa, src);
+                        vq[u] = base + lane < wend;
+                        // segment of base + 32
+                        const int cnt = __popc(__ballot_sync(kFull, rel <= 32));
+                        int ns = s + cnt - 1;
+                        if (cnt == 32 && s + 32 <= nE && sm.off[s + 32] <= base + 32) ns = s + 32;
+                        s = ns < nE - 1 ? ns : nE - 1;
+                        base += 32;
+                        so = sm.off[s];
+                        se = sm.off[s + 1];
+                        sbs = sm.bs[s];
+                        sa = sm.a[s];
+                    }
+                }
+            }
+            Item it[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (vq[u]) it[u] = load(tq[u]);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (vq[u]) apply(it[u], aq[u]);
+        }
+    }
+    __syncthreads();
+}
+
+// expand_tile over A entries [j0, j1) in tiles of kT; seg(j, bs, len, a)
+// gives the segment and multiplier of entry j.
+template <int kT, typename Acc, int kUnroll, class Seg, class Load, class Apply>
+__device__ __forceinline__ void block_expand(int j0, int j1, ExpandTile<kT, Acc>& sm, Seg&& seg,
+                                             Load&& load, Apply&& apply) {
+    for (int tb = j0; tb < j1; tb += kT) {
+        const int j = tb + threadIdx.x;
+        int bs = 0, len = 0;
+        Acc a = Acc(0);
+        if (j < j1) seg(j, bs, len, a);
+        expand_tile<kT, Acc, kUnroll>(sm, bs, len, a, load, apply);
+    }
+}
+
 }  // namespace spg

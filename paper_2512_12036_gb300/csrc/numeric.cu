@@ -41,6 +41,11 @@ __device__ __forceinline__ void hash_add(int* keys, Acc* vals, int bits, int key
     set_status(ctl, ST_INTERNAL);
 }
 
+struct KeyVal {
+    int key;
+    float v;
+};
+
 __device__ __forceinline__ bool key_in(int key, const CsrDev& B, Ctl* ctl) {
     if ((unsigned)key >= (unsigned)B.cols) {
         set_status(ctl, ST_INVALID);
@@ -209,8 +214,8 @@ __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev
     int* keys = reinterpret_cast<int*>(sm_raw + sizeof(Acc) * (1u << max_bits));
     __shared__ int s_idx;
     __shared__ int scratch[33];
+    __shared__ ExpandTile<kNumBlockThreads, Acc> tile;
     const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
         __syncthreads();
@@ -231,12 +236,16 @@ __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev
         __syncthreads();
         int rs, re;
         row_extent(A, row, rs, re, ctl);
-        warp_expand(A, B, rs + warp * 32, re, 32 * nwarps, ctl, [&](int t, int ja) {
-            const int key = B.col[t];
-            if (key_in(key, B, ctl))
-                hash_add<Acc>(keys, vals, bits, key, (Acc)A.val[ja] * (Acc)B.val[t], ctl);
-        });
-        __syncthreads();
+        block_expand<kNumBlockThreads, Acc, 2>(
+            rs, re, tile,
+            [&](int j, int& bs, int& len, Acc& a) {
+                a_entry(A, B, j, bs, len, ctl);
+                a = (Acc)A.val[j];
+            },
+            [&](int t) { return KeyVal{B.col[t], B.val[t]}; },
+            [&](KeyVal kv, Acc a) {
+                if (key_in(kv.key, B, ctl)) hash_add<Acc>(keys, vals, bits, kv.key, a * (Acc)kv.v, ctl);
+            });
         // stable in-place compaction, 4 slots per thread per round
         int n = 0;
         const int per_round = blockDim.x * 4;
@@ -311,26 +320,94 @@ __global__ void k_bpanel(CsrDev B, int P, int PW, int* tab, Ctl* ctl) {
     }
 }
 
-template <typename Acc>
-__global__ void __launch_bounds__(kNumDenseThreads) k_num_dense(CsrDev A, CsrDev B,
-                                                                const int* map, Ctl* ctl,
-                                                                const int* rptC, int row_begin,
-                                                                int* colC, float* valC, int bin_lo,
-                                                                int bin_hi, int tier,
-                                                                const int* tab, int P, int PW) {
+// Dense-panel accumulation of heavy rows. A pass covers W columns: a value
+// array and an occupancy bitmap in shared memory; each product is one
+// atomicOr and one fp32 atomicAdd; the pass is emitted in column order.
+//
+// kMode 0 (rows where at most fp32_max_terms products can meet in an entry):
+//   fp32 values, W = 3 table panels.
+// kMode 1 (rows with more A entries): the row's A entries are taken in
+//   groups of kGroup (<= 165) entries. Inside a group at most kGroup
+//   products meet in an entry, so fp32 accumulation stays within
+//   gamma_kGroup of sum|a||b|; after each group its touched columns are
+//   added into an fp64 array and cleared. With the final rounding to fp32
+//   the total stays below 1e-5 * sum|a||b|, using fp32 shared-memory
+//   atomics only (fp64 shared atomics run ~3.5x slower and collapse under
+//   contention on hub columns). W = 1 table panel.
+//
+// A row with at most kNumDenseThreads A entries keeps each entry's B row,
+// multiplier and current panel boundary in registers of "its" thread, and
+// prefetches the next boundary before the pass runs. Longer rows re-read
+// their entries (and the panel table) in tiles every pass.
+constexpr int kGroup = 160;
+
+template <int kMode>
+__global__ void __launch_bounds__(kNumDenseThreads, 1) k_num_dense(CsrDev A, CsrDev B,
+                                                                   const int* map, Ctl* ctl,
+                                                                   const int* rptC, int row_begin,
+                                                                   int* colC, float* valC,
+                                                                   int bin_lo, int bin_hi,
+                                                                   int tier, const int* tab, int P,
+                                                                   int PW) {
+    constexpr int kPanelsPerPass = kMode == 0 ? 3 : 1;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    Acc* vals = reinterpret_cast<Acc*>(sm_raw);
-    unsigned* bm = reinterpret_cast<unsigned*>(sm_raw + sizeof(Acc) * PW);
+    const int W = PW * kPanelsPerPass;                 // columns per pass
+    const int nwords_pass = W >> 5;
+    double* acc = reinterpret_cast<double*>(sm_raw);   // kMode 1 only
+    float* st = reinterpret_cast<float*>(sm_raw + (kMode == 1 ? sizeof(double) * W : 0));
+    unsigned* bm = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(st) + sizeof(float) * W);
+    unsigned* gbm = bm + nwords_pass;                   // kMode 1 only
     __shared__ int s_idx;
     __shared__ int scratch[33];
+    __shared__ ExpandTile<kNumDenseThreads, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
     if (begin >= end) return;
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int nwords_pw = PW >> 5;
-    for (int i = threadIdx.x; i < PW; i += blockDim.x) vals[i] = Acc(0);
-    for (int i = threadIdx.x; i < nwords_pw; i += blockDim.x) bm[i] = 0u;
+    const int wpt = (nwords_pass + kNumDenseThreads - 1) / kNumDenseThreads;   // words per thread
+    const int w0 = threadIdx.x * wpt;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        st[i] = 0.f;
+        if (kMode == 1) acc[i] = 0.0;
+    }
+    for (int i = threadIdx.x; i < nwords_pass; i += blockDim.x) {
+        bm[i] = 0u;
+        if (kMode == 1) gbm[i] = 0u;
+    }
     const bool use_tab = tab != nullptr && ctl->b_unsorted == 0;
-    const int npanels = (int)((B.cols + (long long)PW - 1) / PW);
+    const int npass = (int)((B.cols + (long long)W - 1) / W);
+    const long long stride = P + 1;
+    unsigned* obm = kMode == 1 ? gbm : bm;             // bitmap the products mark
+
+    int c0 = 0, span = 0;
+    auto load = [&](int t) { return KeyVal{B.col[t], B.val[t]}; };
+    auto apply = [&](KeyVal kv, float a) {
+        if (!key_in(kv.key, B, ctl)) return;
+        const int kk = kv.key - c0;
+        if (kk >= 0 && kk < span) {
+            atomicOr(&obm[kk >> 5], 1u << (kk & 31));
+            atomicAdd(&st[kk], a * kv.v);
+        } else if (use_tab) {
+            set_status(ctl, ST_INTERNAL);
+        }
+    };
+    // kMode 1: move this group's sums into fp64 (thread owns words [w0, w0+wpt))
+    auto flush = [&]() {
+        for (int q = 0; q < wpt; ++q) {
+            const int w = w0 + q;
+            if (w >= nwords_pass) break;
+            unsigned g = gbm[w];
+            if (!g) continue;
+            bm[w] |= g;
+            gbm[w] = 0u;
+            while (g) {
+                const int kk = w * 32 + __ffs(g) - 1;
+                g &= g - 1;
+                acc[kk] += (double)st[kk];
+                st[kk] = 0.f;
+            }
+        }
+        __syncthreads();
+    };
+
     for (;;) {
         if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
         __syncthreads();
@@ -343,79 +420,108 @@ __global__ void __launch_bounds__(kNumDenseThreads) k_num_dense(CsrDev A, CsrDev
         const int nnz_row = rptC[r + 1] - out;
         int rs, re;
         row_extent(A, row, rs, re, ctl);
+        const int na = re - rs;
+        const bool cached = use_tab && na <= kNumDenseThreads;
+        int myk = -1, cur = 0, nxt = 0;
+        float mya = 0.f;
+        if (cached && (int)threadIdx.x < na) {
+            const int j = rs + threadIdx.x;
+            const int k = A.col[j];
+            if ((unsigned)k < (unsigned)B.rows) {
+                myk = k;
+                mya = A.val[j];
+                cur = tab[(long long)k * stride];
+                nxt = tab[(long long)k * stride + (kPanelsPerPass < P ? kPanelsPerPass : P)];
+            } else {
+                set_status(ctl, ST_INVALID);
+            }
+        }
         int written = 0;
-        for (int p = 0; p < npanels; ++p) {
-            const int c0 = p * PW;
-            const int span = (int)(B.cols - (long long)c0 < PW ? B.cols - (long long)c0 : PW);
-            // products of this panel
-            const int lane = lane_id();
-            for (int base = rs + warp * 32; base < re; base += 32 * nwarps) {
-                const int j = base + lane;
+        for (int pass = 0; pass < npass; ++pass) {
+            c0 = pass * W;
+            span = (int)(B.cols - (long long)c0 < W ? B.cols - (long long)c0 : W);
+            const int p0 = pass * kPanelsPerPass;
+            const int p1 = p0 + kPanelsPerPass < P ? p0 + kPanelsPerPass : P;
+            if (cached) {
+                int nxt2 = 0;
+                if (myk >= 0 && pass + 1 < npass) {
+                    const int pn = p1 + kPanelsPerPass < P ? p1 + kPanelsPerPass : P;
+                    nxt2 = tab[(long long)myk * stride + pn];
+                }
                 int bs = 0, len = 0;
-                Acc a = Acc(0);
-                if (j < re) {
-                    a_entry(A, B, j, bs, len, ctl);
-                    a = (Acc)A.val[j];
-                    if (use_tab && len > 0) {
-                        const int k = A.col[j];
-                        const int* tk = tab + (long long)k * (P + 1);
-                        const int ps = tk[p], pe = tk[p + 1];
-                        if (ps >= bs && pe >= ps && pe <= bs + len) {
-                            bs = ps;
-                            len = pe - ps;
-                        } else {
-                            set_status(ctl, ST_INTERNAL);
-                            len = 0;
-                        }
+                if (myk >= 0) {
+                    if (cur < 0 || nxt < cur || (long long)nxt > B.nnz) set_status(ctl, ST_INTERNAL);
+                    else {
+                        bs = cur;
+                        len = nxt - cur;
                     }
                 }
-                const int incl = warp_incl_scan(len);
-                const int excl = incl - len;
-                const int total = __shfl_sync(kFull, incl, 31);
-                for (int p0 = 0; p0 < total; p0 += 32) {
-                    const int pp = p0 + lane;
-                    const int s = warp_find_src(excl, pp);
-                    const int sbs = __shfl_sync(kFull, bs, s);
-                    const int sex = __shfl_sync(kFull, excl, s);
-                    const Acc sa = __shfl_sync(kFull, a, s);
-                    if (pp < total) {
-                        const int t = sbs + (pp - sex);
-                        const int key = B.col[t];
-                        if (key_in(key, B, ctl)) {
-                            const int kk = key - c0;
-                            if (kk >= 0 && kk < span) {
-                                const unsigned bit = 1u << (kk & 31);
-                                unsigned* wp = &bm[kk >> 5];
-                                if (!(*(volatile unsigned*)wp & bit)) atomicOr(wp, bit);
-                                atomicAdd(&vals[kk], sa * (Acc)B.val[t]);
-                            } else if (use_tab) {
+                if (kMode == 0) {
+                    expand_tile<kNumDenseThreads, float, 4>(tile, bs, len, mya, load, apply);
+                } else {
+                    for (int g0 = 0; g0 < na; g0 += kGroup) {
+                        const bool mine = (int)threadIdx.x >= g0 && (int)threadIdx.x < g0 + kGroup;
+                        expand_tile<kNumDenseThreads, float, 4>(tile, bs, mine ? len : 0, mya, load,
+                                                                apply);
+                        flush();
+                    }
+                }
+                cur = nxt;
+                nxt = nxt2;
+            } else {
+                const int T = kMode == 0 ? kNumDenseThreads : kGroup;
+                for (int tb = rs; tb < re; tb += T) {
+                    const int j = tb + threadIdx.x;
+                    int bs = 0, len = 0;
+                    float a = 0.f;
+                    if ((int)threadIdx.x < T && j < re) {
+                        a_entry(A, B, j, bs, len, ctl);
+                        a = A.val[j];
+                        if (use_tab && len > 0) {
+                            const int* tk = tab + (long long)A.col[j] * stride;
+                            const int ps = tk[p0], pe = tk[p1];
+                            if (ps >= bs && pe >= ps && pe <= bs + len) {
+                                bs = ps;
+                                len = pe - ps;
+                            } else {
                                 set_status(ctl, ST_INTERNAL);
+                                len = 0;
                             }
                         }
                     }
+                    expand_tile<kNumDenseThreads, float, 4>(tile, bs, len, a, load, apply);
+                    if (kMode == 1) flush();
                 }
             }
-            __syncthreads();
-            // emit this panel in column order
+            // emit this pass in column order: thread t owns words [w0, w0+wpt)
             const int nw = (span + 31) >> 5;
-            const unsigned word = (int)threadIdx.x < nw ? bm[threadIdx.x] : 0u;
+            int cnt = 0;
+            for (int q = 0; q < wpt; ++q)
+                if (w0 + q < nw) cnt += __popc(bm[w0 + q]);
             int tot;
-            int pos = written + block_excl_scan(__popc(word), scratch, &tot);
-            if ((int)threadIdx.x < nw) {
-                unsigned wbits = word;
+            int pos = written + block_excl_scan(cnt, scratch, &tot);
+            for (int q = 0; q < wpt; ++q) {
+                const int w = w0 + q;
+                if (w >= nw) break;
+                unsigned wbits = bm[w];
                 while (wbits) {
-                    const int b = __ffs(wbits) - 1;
+                    const int kk = w * 32 + __ffs(wbits) - 1;
                     wbits &= wbits - 1;
-                    const int kk = threadIdx.x * 32 + b;
-                    const Acc v = vals[kk];
-                    vals[kk] = Acc(0);
+                    float v;
+                    if (kMode == 1) {
+                        v = (float)acc[kk];
+                        acc[kk] = 0.0;
+                    } else {
+                        v = st[kk];
+                        st[kk] = 0.f;
+                    }
                     if (pos < nnz_row) {
                         colC[out + pos] = c0 + kk;
-                        valC[out + pos] = (float)v;
+                        valC[out + pos] = v;
                     }
                     ++pos;
                 }
-                bm[threadIdx.x] = 0u;
+                bm[w] = 0u;
             }
             written += tot;
             __syncthreads();
@@ -430,8 +536,11 @@ static size_t num_warp_smem(size_t acc) { return (acc + 4) * kWarpsPerBlockNW * 
 static size_t num_block_smem(const spgemm_plan* p, size_t acc) {
     return (acc + 4) * pow2_ceil(2u * (unsigned)p->opts.block_max_nnz);
 }
-static size_t num_dense_smem(const spgemm_plan* p, size_t acc) {
-    return acc * p->opts.panel_cols + p->opts.panel_cols / 8;
+// kMode 0: fp32 values and a bitmap over three table panels; kMode 1: fp64
+// values, fp32 group sums and two bitmaps over one panel
+static size_t num_dense_smem(const spgemm_plan* p, int mode) {
+    const size_t W = (size_t)p->opts.panel_cols * (mode == 0 ? 3 : 1);
+    return mode == 0 ? 4 * W + W / 8 : 12 * W + W / 4;
 }
 
 void occupancy_numeric(spgemm_plan* p) {
@@ -445,8 +554,8 @@ void occupancy_numeric(spgemm_plan* p) {
         {(const void*)k_num_warp<double>, kWarpsPerBlockNW * 32, num_warp_smem(8), &p->occ_num_warp64},
         {(const void*)k_num_block<float>, kNumBlockThreads, num_block_smem(p, 4), &p->occ_num_block32},
         {(const void*)k_num_block<double>, kNumBlockThreads, num_block_smem(p, 8), &p->occ_num_block64},
-        {(const void*)k_num_dense<float>, kNumDenseThreads, num_dense_smem(p, 4), &p->occ_num_dense32},
-        {(const void*)k_num_dense<double>, kNumDenseThreads, num_dense_smem(p, 8), &p->occ_num_dense64},
+        {(const void*)k_num_dense<0>, kNumDenseThreads, num_dense_smem(p, 0), &p->occ_num_dense32},
+        {(const void*)k_num_dense<1>, kNumDenseThreads, num_dense_smem(p, 1), &p->occ_num_dense64},
     };
     for (auto& k : ks) {
         cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
@@ -498,11 +607,11 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits));
     const int PW = w.panel_cols;
     SPG_LAUNCH(p, K_NUM_DENSE32, s,
-               k_num_dense<float><<<sms * p->occ_num_dense32, kNumDenseThreads, num_dense_smem(p, 4), s>>>(
+               k_num_dense<0><<<sms * p->occ_num_dense32, kNumDenseThreads, num_dense_smem(p, 0), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
                    NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW));
     SPG_LAUNCH(p, K_NUM_DENSE64, s,
-               k_num_dense<double><<<sms * p->occ_num_dense64, kNumDenseThreads, num_dense_smem(p, 8), s>>>(
+               k_num_dense<1><<<sms * p->occ_num_dense64, kNumDenseThreads, num_dense_smem(p, 1), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
                    NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW));
 }

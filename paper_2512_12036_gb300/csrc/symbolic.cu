@@ -14,7 +14,7 @@
 
 namespace spg {
 
-constexpr int kSymDenseWords = 48 * 1024;   // 192 KB bitmap
+constexpr int kSymDenseWords = 48 * 1024;   // 192 KB bitmap (1.5M columns per pass)
 
 __device__ __forceinline__ int hash_insert(int* table, int bits, int key, Ctl* ctl) {
     const unsigned mask = (1u << bits) - 1u;
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev
     extern __shared__ int table[];
     __shared__ int s_idx;
     __shared__ int red[33];
+    __shared__ ExpandTile<kSymBlockThreads, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
         __syncthreads();
@@ -136,17 +136,20 @@ __global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev
         int rs, re;
         row_extent(A, row, rs, re, ctl);
         int cnt = 0;
-        warp_expand(A, B, rs + warp * 32, re, 32 * nwarps, ctl, [&](int t, int) {
-            const int key = B.col[t];
-            if (key_ok(key, B, ctl)) cnt += hash_insert(table, bits, key, ctl);
-        });
+        block_expand<kSymBlockThreads, float, 2>(
+            rs, re, tile,
+            [&](int j, int& bs, int& len, float&) { a_entry(A, B, j, bs, len, ctl); },
+            [&](int t) { return B.col[t]; },
+            [&](int key, float) {
+                if (key_ok(key, B, ctl)) cnt += hash_insert(table, bits, key, ctl);
+            });
         cnt = block_sum(cnt, red);
         if (threadIdx.x == 0) row_nnz[row] = cnt;
     }
 }
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSymDenseThreads) k_sym_dense(CsrDev A, CsrDev B,
+__global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, CsrDev B,
                                                                 const int* map, Ctl* ctl,
                                                                 int* row_nnz, int bin_lo,
                                                                 int bin_hi, int tier,
@@ -154,8 +157,8 @@ __global__ void __launch_bounds__(kSymDenseThreads) k_sym_dense(CsrDev A, CsrDev
     extern __shared__ unsigned bm[];
     __shared__ int s_idx;
     __shared__ int red[33];
+    __shared__ ExpandTile<kSymDenseThreads, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const long long span_max = (long long)nwords * 32;
     for (;;) {
         if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
@@ -172,16 +175,16 @@ __global__ void __launch_bounds__(kSymDenseThreads) k_sym_dense(CsrDev A, CsrDev
             const int nw = (span + 31) >> 5;
             for (int q = threadIdx.x; q < nw; q += blockDim.x) bm[q] = 0u;
             __syncthreads();
-            warp_expand(A, B, rs + warp * 32, re, 32 * nwarps, ctl, [&](int t, int) {
-                const int key = B.col[t];
-                if (!key_ok(key, B, ctl)) return;
-                const long long kk = key - c0;
-                if (kk < 0 || kk >= span) return;
-                const unsigned bit = 1u << (kk & 31);
-                unsigned* wp = &bm[kk >> 5];
-                if (!(*(volatile unsigned*)wp & bit)) atomicOr(wp, bit);
-            });
-            __syncthreads();
+            block_expand<kSymDenseThreads, float, 4>(
+                rs, re, tile,
+                [&](int j, int& bs, int& len, float&) { a_entry(A, B, j, bs, len, ctl); },
+                [&](int t) { return B.col[t]; },
+                [&](int key, float) {
+                    if (!key_ok(key, B, ctl)) return;
+                    const long long kk = key - c0;
+                    if (kk < 0 || kk >= span) return;
+                    atomicOr(&bm[kk >> 5], 1u << (kk & 31));
+                });
             int cnt = 0;
             for (int q = threadIdx.x; q < nw; q += blockDim.x) cnt += __popc(bm[q]);
             nnz += block_sum(cnt, red);
@@ -194,7 +197,8 @@ __global__ void __launch_bounds__(kSymDenseThreads) k_sym_dense(CsrDev A, CsrDev
 
 static size_t sym_dense_smem(const spgemm_plan* p) {
     size_t words = kSymDenseWords;
-    const size_t cap = (p->smem_optin > 4096 ? p->smem_optin - 2048 : 4096) / 4;
+    const size_t stat = sizeof(ExpandTile<kSymDenseThreads, float>) + 1024;
+    const size_t cap = (p->smem_optin > stat + 4096 ? p->smem_optin - stat : 4096) / 4;
     if (words > cap) words = cap;
     return words * 4;
 }

@@ -80,6 +80,16 @@ def test_every_tier(plan):
     check_product(plan, A, B)
 
 
+def test_dense_tier_long_a_rows(plan):
+    # heavy rows with more A entries than one block tile (uncached dense path),
+    # fp64 accumulation, ragged last panel
+    B = hub_matrix(3000, 70000, 15, heavy_rows=set(range(0, 3000, 11)), heavy_len=200, light_deg=20)
+    A = hub_matrix(40, 3000, 16, heavy_rows={0, 7, 39}, heavy_len=2500, light_deg=30)
+    nnz = oracle.symbolic(A, B)
+    assert nnz.max() > 8192 and np.diff(A.row_ptr).max() > 1024
+    check_product(plan, A, B)
+
+
 def test_dense_tier_unsorted_b(plan):
     B = hub_matrix(500, 50000, 7, heavy_rows=set(range(0, 500, 3)), heavy_len=400)
     Bu = gen.random_csr(1, 1, 1.0, 0)  # placeholder for type
