@@ -137,6 +137,27 @@ int spgemm_symbolic(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_c
 int spgemm_row_ptr(const spgemm_plan* plan, const int32_t* row_nnz, int32_t n, void* ws,
                    size_t ws_bytes, int32_t* row_ptr, int64_t* total, void* stream);
 
+/* Row pointers without a caller workspace (no counterpart in the paper; an
+ * addition for callers that cannot allocate device memory: plugins whose
+ * host framework owns every device allocation, fixed-budget or real-time
+ * services that forbid allocation after start-up, code that runs where
+ * cudaMalloc is not allowed or would synchronise the device).
+ * Same result and arguments as spgemm_row_ptr, but the scan's scratch lives
+ * in a fixed array compiled into the library (about 132 KB, resident on
+ * every GPU that loads the library until the process exits); the call
+ * allocates nothing. Limits and rules:
+ *  - n <= 2^26 (67,108,864) rows, else SPGEMM_ERR_UNSUPPORTED before any work;
+ *  - the calling thread's current device must be the plan's device;
+ *  - the first call on each device looks up the scratch's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture;
+ *  - every call shares the one scratch array, so calls that overlap on the
+ *    GPU (different streams, threads or processes' streams) race: order
+ *    them on one stream or serialise them.
+ * total [out, host, nullable]: as for spgemm_row_ptr (non-NULL synchronises
+ * and returns SPGEMM_ERR_OVERFLOW past INT32_MAX). */
+int spgemm_row_ptr_static(const spgemm_plan* plan, const int32_t* row_nnz, int32_t n,
+                          int32_t* row_ptr, int64_t* total, void* stream);
+
 /* Accumulation (numeric) phase with sorting (Algorithm 5 and the
  * column-index sorting step): rows [row_begin, row_end) of C.
  * ip_row    [in, device, A.rows]: from spgemm_count.

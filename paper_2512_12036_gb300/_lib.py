@@ -59,6 +59,7 @@ PROTOTYPES = {
     "spgemm_group": (ctypes.c_int, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp, c_sz, c_vp, c_vp, c_vp]),
     "spgemm_symbolic": (ctypes.c_int, [c_vp, _CSR, _CSR, c_vp, c_vp, c_sz, c_vp, _P(c_i64), c_vp]),
     "spgemm_row_ptr": (ctypes.c_int, [c_vp, c_vp, c_i32, c_vp, c_sz, c_vp, _P(c_i64), c_vp]),
+    "spgemm_row_ptr_static": (ctypes.c_int, [c_vp, c_vp, c_i32, c_vp, _P(c_i64), c_vp]),
     "spgemm_numeric": (ctypes.c_int, [c_vp, _CSR, _CSR, c_vp, c_i32, c_i32, c_vp, c_vp, c_sz, c_vp,
                                       c_vp, c_vp]),
     "spgemm": (ctypes.c_int, [c_vp, _CSR, _CSR, c_vp, c_sz, c_vp, c_vp, c_vp, ALLOC_FN, c_vp,

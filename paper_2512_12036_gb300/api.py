@@ -178,6 +178,20 @@ class Plan:
               "spgemm_row_ptr")
         return out, (int(t.value) if total else None)
 
+    def row_ptr_static(self, row_nnz: torch.Tensor, out: torch.Tensor | None = None,
+                       total: bool = False, stream=None):
+        """Row pointers through the entry point that needs no workspace (its
+        scratch is a fixed array inside the library; see spgemm_row_ptr_static)."""
+        n = row_nnz.numel()
+        if out is None:
+            out = torch.empty(n + 1, dtype=torch.int32, device=row_nnz.device)
+        t = ctypes.c_int64()
+        check(_lib.lib().spgemm_row_ptr_static(self.handle, _ptr(row_nnz), n, _ptr(out),
+                                               ctypes.byref(t) if total else None,
+                                               _stream(stream)),
+              "spgemm_row_ptr_static")
+        return out, (int(t.value) if total else None)
+
     def numeric(self, A: DeviceCSR, B: DeviceCSR, ip_row: torch.Tensor, row_ptr_C: torch.Tensor,
                 ws: torch.Tensor, col_C: torch.Tensor, val_C: torch.Tensor, row_begin: int = 0,
                 row_end: int | None = None, stream=None) -> None:
