@@ -75,7 +75,8 @@ typedef struct {
     int32_t block_max_ip;     /* default 16384: allocation phase, block-per-row hash tier */
     int32_t warp_max_nnz;     /* default 512: accumulation phase, warp-per-row hash tier */
     int32_t block_max_nnz;    /* default 8192: accumulation phase, block-per-row hash tier */
-    int32_t panel_cols;       /* default 16384: column panel of the dense heavy-row accumulator */
+    int32_t panel_cols;       /* default 16384 (a power of two, 1024..16384): column panel of
+                                 the dense heavy-row accumulator */
     int32_t reserved[9];
 } spgemm_opts;
 
@@ -169,6 +170,27 @@ int spgemm_numeric(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_cs
                    const int64_t* ip_row, int32_t row_begin, int32_t row_end,
                    const int32_t* row_ptr_C, void* ws, size_t ws_bytes, int32_t* col_C,
                    float* val_C, void* stream);
+
+/* Backward of C = A*B with respect to the stored values (the gradient rule
+ * of the pruned-GNN aggregation, Eq. 3, read per stored value):
+ *   dA[j] = sum_{t in row k of B} dC(i, colB[t]) * valB[t]   for A entry j = (i,k)
+ *           (an SDDMM of dC * B^T sampled at A's pattern),
+ *   dB[t] = sum_{A entries j = (i,k)} valA[j] * dC(i, colB[t])   for B entry t in row k
+ *           (A^T * dC sampled at B's pattern).
+ * row_ptr_C [device, A.rows+1], col_C [device, nnz_C]: C's structure as
+ *   spgemm produced it (rows sorted); it must contain every column a
+ *   product of row i reaches (otherwise SPGEMM_ERR_INVALID on the status).
+ * dC [device, nnz_C]: the gradient on C's stored values.
+ * dA [out, device, A.nnz, nullable], dB [out, device, B.nnz, nullable]:
+ *   fully overwritten; sums are accumulated in fp64 and rounded once.
+ * Workspace: spgemm_backward_workspace_bytes (includes B.nnz + A.nnz fp64
+ * slots). Does not synchronise. C must fit int32 row pointers. */
+int spgemm_backward_workspace_bytes(const spgemm_plan* plan, const spgemm_csr* A,
+                                    const spgemm_csr* B, size_t* bytes);
+int spgemm_backward(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                    const int32_t* row_ptr_C, const int32_t* col_C, int64_t nnz_C,
+                    const float* dC, float* dA, float* dB, void* ws, size_t ws_bytes,
+                    void* stream);
 
 /* Allocation callback for spgemm(): must return device buffers of nnz
  * entries (col and val) and 0, or nonzero to abort. */

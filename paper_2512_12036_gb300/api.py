@@ -66,7 +66,8 @@ class DeviceCSR:
         base = int(rp[0]) if rp.size else 0
         end = int(rp[-1]) if rp.size else 0
         col = self.col[base:end].cpu().numpy()
-        val = self.val[base:end].cpu().numpy() if self.val is not None else np.zeros(0, np.float32)
+        val = (self.val[base:end].detach().cpu().numpy() if self.val is not None
+               else np.zeros(0, np.float32))
         return HostCSR(self.rows, self.cols, (rp - base).astype(np.int32), col, val)
 
     def view_rows(self, r0: int, r1: int) -> "DeviceCSR":
@@ -203,6 +204,35 @@ class Plan:
                                         _ptr(row_ptr_C), _ptr(ws), ws.numel(), _ptr(col_C),
                                         _ptr(val_C), _stream(stream)),
               "spgemm_numeric")
+
+    # ----------------------------------------------------------------- backward
+    def backward_workspace(self, A: DeviceCSR, B: DeviceCSR) -> torch.Tensor:
+        n = ctypes.c_size_t()
+        check(_lib.lib().spgemm_backward_workspace_bytes(self.handle, ctypes.byref(A.struct()),
+                                                         ctypes.byref(B.struct()), ctypes.byref(n)),
+              "spgemm_backward_workspace_bytes")
+        ws = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=A.device)
+        off = (-ws.data_ptr()) % 256
+        ws = ws[off:off + int(n.value)]
+        self.workspace_init(ws)
+        return ws
+
+    def backward(self, A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, dC: torch.Tensor,
+                 need_dA: bool = True, need_dB: bool = True, ws: torch.Tensor | None = None,
+                 stream=None):
+        """Gradients of sum(dC * C) with respect to A's and B's stored values
+        (dA: SDDMM of dC*B^T at A's pattern; dB: A^T*dC at B's pattern)."""
+        if ws is None:
+            ws = self.backward_workspace(A, B)
+        dA = torch.empty(A.nnz, dtype=torch.float32, device=A.device) if need_dA else None
+        dB = torch.empty(B.nnz, dtype=torch.float32, device=A.device) if need_dB else None
+        dC = dC.contiguous().to(torch.float32)
+        check(_lib.lib().spgemm_backward(self.handle, ctypes.byref(A.struct()),
+                                         ctypes.byref(B.struct()), _ptr(C.row_ptr), _ptr(C.col),
+                                         C.nnz, _ptr(dC), _ptr(dA), _ptr(dB), _ptr(ws), ws.numel(),
+                                         _stream(stream)),
+              "spgemm_backward")
+        return dA, dB
 
     # --------------------------------------------------------- diagnostics
     def launches(self) -> int:

@@ -7,6 +7,7 @@
 namespace spg {
 void occupancy_symbolic(spgemm_plan* p);
 void occupancy_numeric(spgemm_plan* p);
+void occupancy_backward(spgemm_plan* p);
 void launch_bpanel(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaStream_t s);
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -52,13 +53,14 @@ WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols) {
 void init_occupancy(spgemm_plan* p) {
     occupancy_symbolic(p);
     occupancy_numeric(p);
+    occupancy_backward(p);
 }
 
 const char* const kKernelNames[K_NUM_KERNELS] = {
     "fill", "check_rpt", "zero_total", "ip_count", "sum", "group_hist", "group_scan",
     "group_scatter", "scan_part", "scan_top", "scan_final", "reset_flag", "bpanel", "sym_esc",
     "sym_warp", "sym_block", "sym_dense", "num_esc", "num_warp32", "num_warp64", "num_block32",
-    "num_block64", "num_dense32", "num_dense64"};
+    "num_block64", "num_dense32", "num_dense64", "backward"};
 
 void prof_begin(const spgemm_plan* p, int kid, cudaStream_t s) {
     (void)kid;
@@ -190,7 +192,7 @@ int spgemm_plan_create(spgemm_plan** out, const spgemm_opts* opts, int device) {
     if (o.block_max_ip < o.warp_max_ip || o.block_max_ip > 32768) return SPGEMM_ERR_INVALID;
     if (o.warp_max_nnz < 1 || o.warp_max_nnz > kWarpTableNum / 2) return SPGEMM_ERR_INVALID;
     if (o.block_max_nnz < o.warp_max_nnz || o.block_max_nnz > 8192) return SPGEMM_ERR_INVALID;
-    if (o.panel_cols < 1024 || o.panel_cols > 16384 || (o.panel_cols & 1023))
+    if (o.panel_cols < 1024 || o.panel_cols > 16384 || (o.panel_cols & (o.panel_cols - 1)))
         return SPGEMM_ERR_INVALID;
     if (o.fp32_max_terms < 0) return SPGEMM_ERR_INVALID;
     int ndev = 0;
@@ -425,6 +427,43 @@ int spgemm(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, vo
     if (rc) return rc;
     WsLayout L = ws_layout(plan, A->rows, B->rows, B->cols);
     return sync_read(ws_ptrs(L, ws, plan->opts.panel_cols).ctl, -1, nullptr, (cudaStream_t)stream);
+}
+
+static size_t backward_ws_bytes(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                                WsLayout* L) {
+    *L = ws_layout(plan, A->rows, B->rows, B->cols);
+    return L->total + backward_extra_bytes(A->nnz, B->nnz);
+}
+
+int spgemm_backward_workspace_bytes(const spgemm_plan* plan, const spgemm_csr* A,
+                                    const spgemm_csr* B, size_t* bytes) {
+    if (!plan || !A || !B || !bytes) return SPGEMM_ERR_INVALID;
+    if (A->rows < 0 || B->rows < 0 || B->cols < 0 || A->nnz < 0 || B->nnz < 0)
+        return SPGEMM_ERR_INVALID;
+    WsLayout L;
+    *bytes = backward_ws_bytes(plan, A, B, &L);
+    return SPGEMM_OK;
+}
+
+int spgemm_backward(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,
+                    const int32_t* row_ptr_C, const int32_t* col_C, int64_t nnz_C,
+                    const float* dC, float* dA, float* dB, void* ws, size_t ws_bytes,
+                    void* stream) {
+    int rc = check_pair(plan, A, B, true);
+    if (rc) return rc;
+    if (nnz_C < 0 || nnz_C > 2147483647ll) return SPGEMM_ERR_INVALID;
+    if (A->rows > 0 && !row_ptr_C) return SPGEMM_ERR_INVALID;
+    if (nnz_C > 0 && (!col_C || !dC)) return SPGEMM_ERR_INVALID;
+    if (A->nnz > 0 && dA == nullptr && dB == nullptr) return SPGEMM_OK;
+    WsLayout L;
+    const size_t need = backward_ws_bytes(plan, A, B, &L);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return SPGEMM_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    double* dB64 = (double*)((char*)ws + L.total);
+    double* dA64 = dB64 + (B->nnz > 0 ? B->nnz : 1);
+    launch_backward(plan, dev_view(A), dev_view(B), row_ptr_C, col_C, dC, dA, dB, w, dB64, dA64, s);
+    return cuda_err(cudaGetLastError());
 }
 
 int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status) {

@@ -150,6 +150,14 @@ __device__ __forceinline__ int bin_of(const GroupArgs& g, int r, bool settle) {
         while (b < g.nthr && k >= g.thr[b]) ++b;
         return b;
     }
+    if (g.phase == 3) {       // backward tiers, by nnz of row r of C
+        const int nc = g.rptC[r + 1] - g.rptC[r];
+        if (nc <= 0) return kSkipBin;
+        if (g.bcols <= kBwdDenseCols) return BW_DENSE;
+        if (nc <= kBwdWarpSlots / 2) return BW_WARP;
+        if (nc <= kBwdBlockSlots / 2) return BW_BLOCK;
+        return BW_PANEL;
+    }
     const int row = g.row_begin + r;
     const long long ip = g.ip[row];
     const int na = g.rptA[row + 1] - g.rptA[row];

@@ -14,7 +14,7 @@ enum KernelId : int {
     K_FILL, K_CHECK_RPT, K_ZERO, K_IP_COUNT, K_SUM, K_GROUP_HIST, K_GROUP_SCAN, K_GROUP_SCATTER,
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_FINAL, K_RESET, K_BPANEL, K_SYM_ESC, K_SYM_WARP, K_SYM_BLOCK,
     K_SYM_DENSE, K_NUM_ESC, K_NUM_WARP32, K_NUM_WARP64, K_NUM_BLOCK32, K_NUM_BLOCK64,
-    K_NUM_DENSE32, K_NUM_DENSE64, K_NUM_KERNELS
+    K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_NUM_KERNELS
 };
 extern const char* const kKernelNames[K_NUM_KERNELS];
 
@@ -67,6 +67,13 @@ enum : int {
     NB_DENSE32_0 = 5, NB_DENSE_N = 16, NB_DENSE64_0 = 21
 };
 
+// Backward tiers (grouping phase 3, by nnz of the row of C): dense lookup
+// when B has few columns, warp hash, block hash, dense column panels.
+constexpr int kBwdDenseCols = 2048;
+constexpr int kBwdWarpSlots = 1024;
+constexpr int kBwdBlockSlots = 16384;
+enum : int { BW_DENSE = 0, BW_WARP = 1, BW_BLOCK = 2, BW_PANEL = 3 };
+
 // Workspace layout: all offsets 256-byte aligned, derived from shapes only.
 struct WsLayout {
     size_t ctl = 0;          // Ctl
@@ -107,6 +114,7 @@ struct GroupArgs {
     const long long* key;      // generic: keys (n)
     const long long* thr;      // generic: thresholds
     int nthr;
+    int bcols;                 // backward: columns of B
     spgemm_opts opts;
 };
 void launch_group(const spgemm_plan* p, const GroupArgs& g, const WsPtrs& w, int* map_out,
@@ -122,6 +130,11 @@ void launch_nnz_total(const spgemm_plan* p, const int* row_nnz, int n, const WsP
 void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
                     int row_begin, int row_end, const int* rptC, const WsPtrs& w, int* colC,
                     float* valC, cudaStream_t s);
+
+void launch_backward(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const int* rptC,
+                     const int* colC, const float* dC, float* dA, float* dB, const WsPtrs& w,
+                     double* dB64, double* dA64, cudaStream_t s);
+size_t backward_extra_bytes(long long a_nnz, long long b_nnz);
 
 void init_occupancy(spgemm_plan* p);
 
