@@ -207,6 +207,25 @@ int spgemm(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, vo
            size_t ws_bytes, int64_t* ip_row, int32_t* row_nnz, int32_t* row_ptr_C,
            spgemm_alloc_fn alloc, void* alloc_ctx, int64_t* nnz_C, void* stream);
 
+/* The whole product without host synchronisation or allocation, so that it
+ * can be captured in a CUDA graph and replayed (e.g. thousands of small,
+ * uneven products stacked as one block-diagonal A and one stacked B: the
+ * result is the stacked per-problem products, since (blockdiag A_b) *
+ * (stacked B_b) = stacked (A_b * B_b)). Same phases as spgemm().
+ * ip_row [device, A.rows int64], row_nnz [device, A.rows int32]: scratch
+ *   (left holding IP and nnz per row).
+ * row_ptr_C [out, device, A.rows+1], col_C / val_C [out, device, capacity]:
+ *   caller-sized output; capacity <= INT32_MAX.
+ * nnz_C [out, DEVICE int64]: the number of entries of C.
+ * When C needs more than `capacity` entries, nothing is written to
+ * col_C/val_C, *nnz_C still holds the size, and the status word records
+ * SPGEMM_ERR_BUDGET (read it with spgemm_status after the stream is done).
+ * The workspace must be initialised (spgemm_workspace_init) before first use;
+ * the status word is sticky until read. */
+int spgemm_batched(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, void* ws,
+                   size_t ws_bytes, int64_t* ip_row, int32_t* row_nnz, int32_t* row_ptr_C,
+                   int32_t* col_C, float* val_C, int64_t capacity, int64_t* nnz_C, void* stream);
+
 /* Synchronise `stream`, read and clear the workspace's device status word;
  * *status receives the SPGEMM_ERR_* code it maps to (SPGEMM_OK if clean). */
 int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status);

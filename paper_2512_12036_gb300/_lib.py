@@ -67,6 +67,8 @@ PROTOTYPES = {
     "spgemm_backward_workspace_bytes": (ctypes.c_int, [c_vp, _CSR, _CSR, _P(c_sz)]),
     "spgemm_backward": (ctypes.c_int, [c_vp, _CSR, _CSR, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp,
                                        c_sz, c_vp]),
+    "spgemm_batched": (ctypes.c_int, [c_vp, _CSR, _CSR, c_vp, c_sz, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                      c_i64, c_vp, c_vp]),
     "spgemm_status": (ctypes.c_int, [c_vp, c_vp, c_vp, _P(ctypes.c_int)]),
     "spgemm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "spgemm_profile_enable": (ctypes.c_int, [c_vp, ctypes.c_int]),

@@ -8,8 +8,6 @@ namespace spg {
 void occupancy_symbolic(spgemm_plan* p);
 void occupancy_numeric(spgemm_plan* p);
 void occupancy_backward(spgemm_plan* p);
-void launch_bpanel(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaStream_t s);
-
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long long b_cols) {
@@ -60,7 +58,7 @@ const char* const kKernelNames[K_NUM_KERNELS] = {
     "fill", "check_rpt", "zero_total", "ip_count", "sum", "group_hist", "group_scan",
     "group_scatter", "scan_part", "scan_top", "scan_final", "reset_flag", "bpanel", "sym_esc",
     "sym_warp", "sym_block", "sym_dense", "num_esc", "num_warp32", "num_warp64", "num_block32",
-    "num_block64", "num_dense32", "num_dense64", "backward"};
+    "num_block64", "num_dense32", "num_dense64", "backward", "guard"};
 
 void prof_begin(const spgemm_plan* p, int kid, cudaStream_t s) {
     (void)kid;
@@ -138,6 +136,7 @@ static int check_ws(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_c
 
 static int map_status(int bits) {
     if (bits & ST_INVALID) return SPGEMM_ERR_INVALID;
+    if (bits & ST_BUDGET) return SPGEMM_ERR_BUDGET;
     if (bits & ST_OVERFLOW) return SPGEMM_ERR_OVERFLOW;
     if (bits & ST_TIMEOUT) return SPGEMM_ERR_TIMEOUT;
     if (bits & ST_UNSUPPORTED) return SPGEMM_ERR_UNSUPPORTED;
@@ -427,6 +426,31 @@ int spgemm(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, vo
     if (rc) return rc;
     WsLayout L = ws_layout(plan, A->rows, B->rows, B->cols);
     return sync_read(ws_ptrs(L, ws, plan->opts.panel_cols).ctl, -1, nullptr, (cudaStream_t)stream);
+}
+
+int spgemm_batched(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, void* ws,
+                   size_t ws_bytes, int64_t* ip_row, int32_t* row_nnz, int32_t* row_ptr_C,
+                   int32_t* col_C, float* val_C, int64_t capacity, int64_t* nnz_C, void* stream) {
+    int rc = check_pair(plan, A, B, true);
+    if (rc) return rc;
+    if (capacity < 0 || capacity > 2147483647ll) return SPGEMM_ERR_INVALID;
+    if (!nnz_C || !row_ptr_C) return SPGEMM_ERR_INVALID;
+    if (A->rows > 0 && (!ip_row || !row_nnz)) return SPGEMM_ERR_INVALID;
+    if (capacity > 0 && (!col_C || !val_C)) return SPGEMM_ERR_INVALID;
+    WsLayout L;
+    rc = check_ws(plan, A, B, ws, ws_bytes, &L);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    CsrDev dA = dev_view(A), dB = dev_view(B);
+    launch_ip_count(plan, dA, dB, (long long*)ip_row, w, s);
+    launch_symbolic(plan, dA, dB, (const long long*)ip_row, w, row_nnz, s);
+    launch_bpanel(plan, dB, w, s);
+    launch_row_ptr(plan, row_nnz, A->rows, w, row_ptr_C, s);
+    launch_copy_total(plan, w, 2, (long long*)nnz_C, s);
+    launch_numeric(plan, dA, dB, (const long long*)ip_row, 0, A->rows, row_ptr_C, w, col_C, val_C,
+                   s, capacity);
+    return cuda_err(cudaGetLastError());
 }
 
 static size_t backward_ws_bytes(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B,

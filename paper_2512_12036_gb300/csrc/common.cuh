@@ -19,7 +19,8 @@ enum : int {
     ST_INTERNAL = 2,   // a capacity guard tripped (table full, count mismatch)
     ST_OVERFLOW = 4,   // a 32-bit result overflowed
     ST_TIMEOUT = 8,    // a bounded wait gave up
-    ST_UNSUPPORTED = 16
+    ST_UNSUPPORTED = 16,
+    ST_BUDGET = 32     // the result exceeds the caller's output capacity
 };
 
 // Control block at the start of every workspace (256-byte aligned).

@@ -14,7 +14,7 @@ enum KernelId : int {
     K_FILL, K_CHECK_RPT, K_ZERO, K_IP_COUNT, K_SUM, K_GROUP_HIST, K_GROUP_SCAN, K_GROUP_SCATTER,
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_FINAL, K_RESET, K_BPANEL, K_SYM_ESC, K_SYM_WARP, K_SYM_BLOCK,
     K_SYM_DENSE, K_NUM_ESC, K_NUM_WARP32, K_NUM_WARP64, K_NUM_BLOCK32, K_NUM_BLOCK64,
-    K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_NUM_KERNELS
+    K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_GUARD, K_NUM_KERNELS
 };
 extern const char* const kKernelNames[K_NUM_KERNELS];
 
@@ -127,9 +127,14 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
                      const WsPtrs& w, int* row_nnz, cudaStream_t s);
 void launch_nnz_total(const spgemm_plan* p, const int* row_nnz, int n, const WsPtrs& w, cudaStream_t s);
 
+// capacity >= 0: the tiers run only if rptC[n] <= capacity and no overflow
+// was flagged (otherwise ST_BUDGET is recorded and nothing is written).
 void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
                     int row_begin, int row_end, const int* rptC, const WsPtrs& w, int* colC,
-                    float* valC, cudaStream_t s);
+                    float* valC, cudaStream_t s, long long capacity = -1);
+void launch_bpanel(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaStream_t s);
+void launch_copy_total(const spgemm_plan* p, const WsPtrs& w, int which, long long* dst,
+                       cudaStream_t s);
 
 void launch_backward(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const int* rptC,
                      const int* colC, const float* dC, float* dA, float* dB, const WsPtrs& w,

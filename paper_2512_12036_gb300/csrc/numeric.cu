@@ -575,9 +575,26 @@ void launch_bpanel(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaS
     SPG_LAUNCH(p, K_BPANEL, s, k_bpanel<<<(int)blocks, 256, 0, s>>>(B, w.panels, w.panel_cols, w.bpanel, w.ctl));
 }
 
+// Output-capacity guard of the graph-capturable path: empties every bin
+// when C does not fit (or its row pointers overflowed), so no tier writes.
+__global__ void k_cap_guard(const int* rptC, int n, long long capacity, Ctl* ctl) {
+    const bool bad = (ctl->status & ST_OVERFLOW) || (long long)rptC[n] > capacity || rptC[n] < 0;
+    if (bad) {
+        for (int b = threadIdx.x; b <= kNumBins; b += blockDim.x) ctl->bin_off[b] = 0;
+        if (threadIdx.x == 0) set_status(ctl, ST_BUDGET);
+    }
+}
+
+__global__ void k_copy_total(const Ctl* ctl, int which, long long* dst) { *dst = ctl->totals[which]; }
+
+void launch_copy_total(const spgemm_plan* p, const WsPtrs& w, int which, long long* dst,
+                       cudaStream_t s) {
+    SPG_LAUNCH(p, K_GUARD, s, k_copy_total<<<1, 1, 0, s>>>(w.ctl, which, dst));
+}
+
 void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
                     int row_begin, int row_end, const int* rptC, const WsPtrs& w, int* colC,
-                    float* valC, cudaStream_t s) {
+                    float* valC, cudaStream_t s, long long capacity) {
     GroupArgs g{};
     g.phase = 1;
     g.row_begin = row_begin;
@@ -588,6 +605,8 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     g.opts = p->opts;
     launch_group(p, g, w, w.map, nullptr, s);
     if (g.n == 0) return;
+    if (capacity >= 0)
+        SPG_LAUNCH(p, K_GUARD, s, k_cap_guard<<<1, 64, 0, s>>>(rptC, g.n, capacity, w.ctl));
     const int sms = p->num_sms;
     SPG_LAUNCH(p, K_NUM_ESC, s, k_num_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_ESC));
     SPG_LAUNCH(p, K_NUM_WARP32, s,
