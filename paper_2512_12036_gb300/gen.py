@@ -48,8 +48,11 @@ def csr_from_coo(rows: int, cols: int, r: np.ndarray, c: np.ndarray, v: np.ndarr
     r = np.asarray(r, dtype=np.int64)
     c = np.asarray(c, dtype=np.int64)
     v = np.asarray(v, dtype=np.float32)
-    if sort:
-        order = np.lexsort((c, r))
+    if sort and r.size:
+        if cols > 0 and rows * cols < (1 << 62):
+            order = np.argsort(r * cols + c, kind="stable")
+        else:
+            order = np.lexsort((c, r))
         r, c, v = r[order], c[order], v[order]
     counts = np.bincount(r, minlength=rows) if r.size else np.zeros(rows, dtype=np.int64)
     row_ptr = np.zeros(rows + 1, dtype=np.int64)
@@ -77,13 +80,25 @@ def _undirected_to_csr(n: int, u: np.ndarray, v: np.ndarray, w: np.ndarray,
     return csr_from_coo(n, n, rr, cc, ww)
 
 
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (sort + neighbour compare; faster here than
+    numpy's hash-based unique on tens of millions of int64 keys)."""
+    a = np.sort(a)
+    if a.size == 0:
+        return a
+    keep = np.empty(a.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
 def _unique_pairs(n: int, u: np.ndarray, v: np.ndarray):
     """Unique unordered pairs with u != v, returned as (lo, hi) sorted by key."""
     keep = u != v
     u, v = u[keep], v[keep]
     lo = np.minimum(u, v).astype(np.int64)
     hi = np.maximum(u, v).astype(np.int64)
-    key = np.unique(lo * n + hi)
+    key = _sorted_unique(lo * n + hi)
     return key // n, key % n
 
 
@@ -174,7 +189,7 @@ def random_csr(rows: int, cols: int, density: float, seed: int, *, duplicates: b
         nnz = 0
     r = rng.integers(0, max(rows, 1), size=nnz, dtype=np.int64)
     c = rng.integers(0, max(cols, 1), size=nnz, dtype=np.int64)
-    key = np.unique(r * max(cols, 1) + c)
+    key = _sorted_unique(r * max(cols, 1) + c)
     r, c = key // max(cols, 1), key % max(cols, 1)
     if duplicates and r.size:
         extra = rng.integers(0, r.size, size=max(1, r.size // 5))
@@ -248,31 +263,87 @@ def topk_rows(dense: np.ndarray, k: int) -> HostCSR:
     return HostCSR(n, f, row_ptr, cols.reshape(-1).astype(np.int32), vals.reshape(-1))
 
 
+def _topk_columns(dense: np.ndarray, k: int) -> np.ndarray:
+    """Ascending column indices of the k largest values of every row."""
+    try:
+        import torch
+        idx = torch.topk(torch.from_numpy(dense), k, dim=1).indices.numpy()
+    except ImportError:
+        idx = np.argpartition(-dense, k - 1, axis=1)[:, :k]
+    idx = np.sort(idx, axis=1)
+    return idx
+
+
 def gnn_batch(num: int, seed: int, n_min: int = 64, n_max: int = 2048, deg_min: float = 4.0,
-              deg_max: float = 32.0, features: int = 256, k: int = 32) -> GNNBatch:
+              deg_max: float = 32.0, features: int = 256, k: int = 32,
+              chunk_rows: int = 131072) -> GNNBatch:
     """``num`` subgraphs with n log-uniform in [n_min, n_max], average degree
-    U[deg_min, deg_max], sym-normalised A_hat, and X = TopK(N(0,1), k) per row."""
+    U[deg_min, deg_max], sym-normalised A_hat, and X = TopK(N(0,1), k) per row.
+
+    Vectorised over all subgraphs: each graph draws its G(n, p) edge count
+    from the binomial, candidate pairs are drawn uniformly inside every graph
+    and deduplicated, and a uniformly random subset of the distinct pairs of
+    the right size is kept per graph (redrawing for graphs left short)."""
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=num)).astype(np.int64)
     sizes = np.clip(sizes, n_min, n_max)
     degs = rng.uniform(deg_min, deg_max, size=num)
     node_off = np.zeros(num + 1, dtype=np.int64)
     np.cumsum(sizes, out=node_off[1:])
-    rs, cs, vs = [], [], []
-    xr, xc, xv = [], [], []
-    for b in range(num):
-        n = int(sizes[b])
-        Ab = sym_normalised_adjacency(n, min(float(degs[b]), n - 1.0), rng)
-        rr = np.repeat(np.arange(n, dtype=np.int64), np.diff(Ab.row_ptr.astype(np.int64)))
-        rs.append(rr + node_off[b])
-        cs.append(Ab.col.astype(np.int64) + node_off[b])
-        vs.append(Ab.val)
-        Xd = rng.standard_normal((n, features)).astype(np.float32)
-        Xb = topk_rows(Xd, k)
-        xr.append(np.repeat(np.arange(n, dtype=np.int64), k) + node_off[b])
-        xc.append(Xb.col.astype(np.int64))
-        xv.append(Xb.val)
     N = int(node_off[-1])
-    A = csr_from_coo(N, N, np.concatenate(rs), np.concatenate(cs), np.concatenate(vs))
-    X = csr_from_coo(N, features, np.concatenate(xr), np.concatenate(xc), np.concatenate(xv))
+    pairs = sizes * (sizes - 1) // 2
+    p = np.minimum(1.0, degs / np.maximum(sizes - 1, 1))
+    want = rng.binomial(pairs, p).astype(np.int64)
+    done_keys = []
+    pending = np.arange(num)
+    pend_keys = np.zeros(0, dtype=np.int64)
+    have = np.zeros(num, dtype=np.int64)
+    for _ in range(64):
+        if pending.size == 0:
+            break
+        draw = (want[pending] - have[pending]) * 5 // 4 + 16
+        g = np.repeat(pending, draw)
+        n_g = sizes[g]
+        u = (rng.random(g.size) * n_g).astype(np.int64)
+        v = (rng.random(g.size) * n_g).astype(np.int64)
+        ok = u != v
+        g, u, v = g[ok], u[ok], v[ok]
+        lo = np.minimum(u, v) + node_off[g]
+        hi = np.maximum(u, v) + node_off[g]
+        keys = _sorted_unique(np.concatenate([pend_keys, lo * N + hi]))
+        graph_of = np.searchsorted(node_off, keys // N, side="right") - 1
+        cnt = np.bincount(graph_of, minlength=num)
+        have[pending] = cnt[pending]
+        full = cnt[graph_of] >= want[graph_of]
+        # graphs with enough distinct pairs: keep a uniformly random subset
+        fk, fg = keys[full], graph_of[full]
+        prio = rng.integers(0, 1 << 31, size=fk.size, dtype=np.int64)
+        order = np.argsort(fg * (1 << 31) + prio, kind="stable")
+        fk, fg = fk[order], fg[order]
+        first = np.searchsorted(fg, np.arange(num))
+        rank = np.arange(fk.size) - first[fg]
+        done_keys.append(fk[rank < want[fg]])
+        pend_keys = keys[~full]
+        pending = pending[have[pending] < want[pending]]
+    keys = np.concatenate(done_keys) if done_keys else np.zeros(0, dtype=np.int64)
+    lo, hi = keys // N, keys % N
+    ids = np.arange(N, dtype=np.int64)
+    full = np.sort(np.concatenate([lo * N + hi, hi * N + lo, ids * N + ids]))
+    r, c = full // N, full % N
+    deg = np.bincount(r, minlength=N).astype(np.float64)
+    w = (1.0 / np.sqrt(deg[r] * deg[c])).astype(np.float32)
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=N), out=row_ptr[1:])
+    A = HostCSR(N, N, row_ptr.astype(np.int32), c.astype(np.int32), w)
+    kk = min(k, features)
+    xcols = np.empty((N, kk), dtype=np.int32)
+    xvals = np.empty((N, kk), dtype=np.float32)
+    for r0 in range(0, N, chunk_rows):
+        r1 = min(N, r0 + chunk_rows)
+        dense = rng.standard_normal((r1 - r0, features), dtype=np.float32)
+        top = _topk_columns(dense, kk)
+        xcols[r0:r1] = top
+        xvals[r0:r1] = np.take_along_axis(dense, top, axis=1)
+    X = HostCSR(N, features, (np.arange(N + 1, dtype=np.int64) * kk).astype(np.int32),
+                xcols.reshape(-1), xvals.reshape(-1))
     return GNNBatch(num, node_off, A, X, features)
