@@ -226,6 +226,25 @@ int spgemm_batched(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_cs
                    size_t ws_bytes, int64_t* ip_row, int32_t* row_nnz, int32_t* row_ptr_C,
                    int32_t* col_C, float* val_C, int64_t capacity, int64_t* nnz_C, void* stream);
 
+/* One Markov-clustering step after the expansion (Algorithm 6), on the rows
+ * of M^T (a column of M is a row of M^T, so with E = M^T * M^T = (M M)^T
+ * every column operation of the algorithm is a row operation here):
+ *   prune: drop entries with value < theta; top-k: keep the k largest of
+ *   each row (ties: the smaller column; k < 0 keeps all); inflate: v^r;
+ *   normalise: divide by the row sum.
+ * order 0 prunes and cuts on the values, then inflates (the algorithm's
+ * order); order 1 inflates first and decides on the fp32-rounded inflated
+ * values. Decisions are made in fp32, weights and sums in fp64.
+ * E: rows sorted by column (as spgemm produces them). Outputs (device):
+ * row_ptr_out [E.rows+1], col_out / val_out [at least min(E.nnz, E.rows*k)
+ * entries] in column order. nnz_out [host, nullable]: non-NULL synchronises.
+ * Workspace: spgemm_workspace_bytes for a matrix of E.rows rows.
+ * theta <= 0, k < 0, r = 1 is a plain row normalisation (the algorithm's
+ * column-stochastic start on M^T). */
+int spgemm_mcl_step(const spgemm_plan* plan, const spgemm_csr* E, float theta, int32_t k, float r,
+                    int32_t order, void* ws, size_t ws_bytes, int32_t* row_ptr_out,
+                    int32_t* col_out, float* val_out, int64_t* nnz_out, void* stream);
+
 /* Synchronise `stream`, read and clear the workspace's device status word;
  * *status receives the SPGEMM_ERR_* code it maps to (SPGEMM_OK if clean). */
 int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status);

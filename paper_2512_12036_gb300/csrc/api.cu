@@ -58,7 +58,7 @@ const char* const kKernelNames[K_NUM_KERNELS] = {
     "fill", "check_rpt", "zero_total", "ip_count", "sum", "group_hist", "group_scan",
     "group_scatter", "scan_part", "scan_top", "scan_final", "reset_flag", "bpanel", "sym_esc",
     "sym_warp", "sym_block", "sym_dense", "num_esc", "num_warp32", "num_warp64", "num_block32",
-    "num_block64", "num_dense32", "num_dense64", "backward", "guard"};
+    "num_block64", "num_dense32", "num_dense64", "backward", "guard", "mcl"};
 
 void prof_begin(const spgemm_plan* p, int kid, cudaStream_t s) {
     (void)kid;
@@ -488,6 +488,26 @@ int spgemm_backward(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_c
     double* dA64 = dB64 + (B->nnz > 0 ? B->nnz : 1);
     launch_backward(plan, dev_view(A), dev_view(B), row_ptr_C, col_C, dC, dA, dB, w, dB64, dA64, s);
     return cuda_err(cudaGetLastError());
+}
+
+int spgemm_mcl_step(const spgemm_plan* plan, const spgemm_csr* E, float theta, int32_t k, float r,
+                    int32_t order, void* ws, size_t ws_bytes, int32_t* row_ptr_out,
+                    int32_t* col_out, float* val_out, int64_t* nnz_out, void* stream) {
+    if (!plan) return SPGEMM_ERR_INVALID;
+    int rc = check_csr(E, true);
+    if (rc) return rc;
+    if (!row_ptr_out || (order != 0 && order != 1) || !(r > 0.f)) return SPGEMM_ERR_INVALID;
+    if (E->nnz > 0 && (!col_out || !val_out)) return SPGEMM_ERR_INVALID;
+    WsLayout L = ws_layout(plan, E->rows, 0, 0);
+    if (!ws || ws_bytes < L.total || ((uintptr_t)ws & 255)) return SPGEMM_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    launch_mcl_step(plan, dev_view(E), theta, k, (double)r, order, w, row_ptr_out, col_out, val_out,
+                    s);
+    rc = cuda_err(cudaGetLastError());
+    if (rc) return rc;
+    if (nnz_out) return sync_read(w.ctl, 2, nnz_out, s);
+    return SPGEMM_OK;
 }
 
 int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status) {

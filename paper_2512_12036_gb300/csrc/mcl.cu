@@ -1,0 +1,251 @@
+// Markov-clustering matrix step (Algorithm 6) on the rows of M^T: after the
+// expansion E = M^T * M^T (= (M*M)^T), each row of E (a column of M) is
+// pruned (entries below theta dropped), cut to its k largest entries (ties
+// to the smaller column), inflated (v^r) and normalised to sum 1.
+//
+// Keep/drop decisions are taken in fp32 on the value (order 0: prune and
+// top-k first, then inflate) or on the fp32-rounded inflated value (order 1:
+// inflate first). The k-th largest decision value is found by a binary
+// search over order-preserving 32-bit keys, counting with warp or block
+// reductions, so no sort is needed; kept entries keep their column order.
+// Weights and the row sum are fp64; each output is rounded once to fp32.
+// k < 0 keeps every entry that passes the threshold (a plain normalisation
+// when theta <= 0 and r = 1).
+#include "internal.h"
+
+namespace spg {
+
+constexpr int kMclWarpMax = 1024;     // rows up to this length: one warp, 32 entries per lane
+constexpr int kMclThreads = 256;
+constexpr int kMclBlockThreads = 1024;
+
+struct MclParams {
+    float theta;
+    int k;
+    double r;
+    int order;
+};
+
+__device__ __forceinline__ unsigned ord_key(float x) {
+    const unsigned b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ double mcl_weight(float v, double r) {
+    const double d = (double)v;
+    if (r == 2.0) return d * d;
+    if (r == 1.0) return d;
+    return pow(d, r);
+}
+
+__device__ __forceinline__ float mcl_decide(float v, const MclParams& p) {
+    return p.order == 0 ? v : (float)mcl_weight(v, p.r);
+}
+
+// ---------------------------------------------------------------------------
+// One warp per row of length <= kMclWarpMax. kWrite = false: count the kept
+// entries into counts[row]; true: write them at rpt_out[row].
+template <bool kWrite>
+__global__ void __launch_bounds__(kMclThreads) k_mcl_warp(CsrDev E, MclParams prm, int* counts,
+                                                          const int* rpt_out, int* col_out,
+                                                          float* val_out, Ctl* ctl) {
+    constexpr int kPer = kMclWarpMax / 32;
+    const int lane = lane_id();
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long row = gw; row < E.rows; row += nw) {
+        int s, e;
+        row_extent(E, (int)row, s, e, ctl);
+        const int n = e - s;
+        if (n > kMclWarpMax) continue;                       // block kernel's row
+        unsigned key[kPer];
+        int cnt = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int q = s + lane + 32 * i;
+            key[i] = 0u;
+            if (q < e) {
+                const float d = mcl_decide(E.val[q], prm);
+                if (d >= prm.theta) {
+                    key[i] = ord_key(d);
+                    ++cnt;
+                }
+            }
+        }
+        cnt = warp_sum(cnt);
+        const bool cut = prm.k >= 0 && cnt > prm.k;
+        unsigned K = 1u;
+        int need_eq = 0;
+        if (cut) {
+            unsigned lo = 1u, hi = 0xffffffffu;
+            while (lo < hi) {
+                const unsigned mid = lo + (unsigned)(((unsigned long long)hi - lo + 1ull) >> 1);
+                int c = 0;
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) c += key[i] >= mid;
+                if (warp_sum(c) >= prm.k) lo = mid;
+                else hi = mid - 1u;
+            }
+            K = lo;
+            int gt = 0;
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) gt += key[i] > K;
+            need_eq = prm.k - warp_sum(gt);
+        }
+        const int keep_n = cut ? prm.k : cnt;
+        if (!kWrite) {
+            if (lane == 0) counts[row] = keep_n;
+            continue;
+        }
+        // pass 1: kept flags in column order, weight sum
+        unsigned keepmask = 0u;
+        int eq_seen = 0;
+        double wsum = 0.0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const bool cand = key[i] != 0u;
+            bool kp = cand;
+            if (cut) {                               // warp-uniform branch
+                const bool eq = cand && key[i] == K;
+                const unsigned eqb = __ballot_sync(kFull, eq);
+                const int rank = eq_seen + __popc(eqb & lanemask_lt());
+                kp = cand && (key[i] > K || (eq && rank < need_eq));
+                eq_seen += __popc(eqb);
+            }
+            if (kp) {
+                keepmask |= 1u << i;
+                wsum += mcl_weight(E.val[s + lane + 32 * i], prm.r);
+            }
+        }
+        wsum = warp_sum(wsum);
+        // pass 2: write in column order
+        int pos = rpt_out[row];
+        const int pend = rpt_out[row + 1];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const bool kp = (keepmask >> i) & 1u;
+            const unsigned b = __ballot_sync(kFull, kp);
+            if (kp) {
+                const int q = s + lane + 32 * i;
+                const int o = pos + __popc(b & lanemask_lt());
+                if (o < pend) {
+                    col_out[o] = E.col[q];
+                    const double w = mcl_weight(E.val[q], prm.r);
+                    val_out[o] = wsum > 0.0 ? (float)(w / wsum) : 0.f;
+                } else {
+                    set_status(ctl, ST_INTERNAL);
+                }
+            }
+            pos += __popc(b);
+        }
+        if (lane == 0 && pos != pend) set_status(ctl, ST_INTERNAL);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One block per row of length > kMclWarpMax (rows taken by stride).
+template <bool kWrite>
+__global__ void __launch_bounds__(kMclBlockThreads) k_mcl_block(CsrDev E, MclParams prm,
+                                                                int* counts, const int* rpt_out,
+                                                                int* col_out, float* val_out,
+                                                                Ctl* ctl) {
+    __shared__ int red[33];
+    __shared__ double redd[33];
+    __shared__ int scratch[33];
+    for (long long row = blockIdx.x; row < E.rows; row += gridDim.x) {
+        int s, e;
+        row_extent(E, (int)row, s, e, ctl);
+        if (e - s <= kMclWarpMax) continue;
+        auto key_of = [&](int q) -> unsigned {
+            const float d = mcl_decide(E.val[q], prm);
+            return d >= prm.theta ? ord_key(d) : 0u;
+        };
+        int c0 = 0;
+        for (int q = s + threadIdx.x; q < e; q += blockDim.x) c0 += key_of(q) != 0u;
+        const int cnt = block_sum(c0, red);
+        const bool cut = prm.k >= 0 && cnt > prm.k;
+        unsigned K = 1u;
+        int need_eq = 0;
+        if (cut) {
+            unsigned lo = 1u, hi = 0xffffffffu;
+            while (lo < hi) {
+                const unsigned mid = lo + (unsigned)(((unsigned long long)hi - lo + 1ull) >> 1);
+                int c = 0;
+                for (int q = s + threadIdx.x; q < e; q += blockDim.x) c += key_of(q) >= mid;
+                if (block_sum(c, red) >= prm.k) lo = mid;
+                else hi = mid - 1u;
+            }
+            K = lo;
+            int gt = 0;
+            for (int q = s + threadIdx.x; q < e; q += blockDim.x) gt += key_of(q) > K;
+            need_eq = prm.k - block_sum(gt, red);
+        }
+        const int keep_n = cut ? prm.k : cnt;
+        if (!kWrite) {
+            if (threadIdx.x == 0) counts[row] = keep_n;
+            continue;
+        }
+        // chunks of blockDim entries in column order: kept flags, then writes
+        auto kept = [&](int q, unsigned kq, int eq_rank) {
+            if (kq == 0u) return false;
+            if (!cut) return true;
+            if (kq > K) return true;
+            return kq == K && eq_rank < need_eq;
+        };
+        double wpart = 0.0;
+        int eq_seen = 0;
+        for (int base = s; base < e; base += blockDim.x) {
+            const int q = base + threadIdx.x;
+            const unsigned kq = q < e ? key_of(q) : 0u;
+            int eq_tot;
+            const int eq_rank = eq_seen + block_excl_scan((cut && kq == K) ? 1 : 0, scratch, &eq_tot);
+            if (q < e && kept(q, kq, eq_rank)) wpart += mcl_weight(E.val[q], prm.r);
+            eq_seen += eq_tot;
+        }
+        const double wsum = block_sum(wpart, redd);
+        int pos = rpt_out[row];
+        const int pend = rpt_out[row + 1];
+        eq_seen = 0;
+        for (int base = s; base < e; base += blockDim.x) {
+            const int q = base + threadIdx.x;
+            const unsigned kq = q < e ? key_of(q) : 0u;
+            int eq_tot;
+            const int eq_rank = eq_seen + block_excl_scan((cut && kq == K) ? 1 : 0, scratch, &eq_tot);
+            eq_seen += eq_tot;
+            const bool kp = q < e && kept(q, kq, eq_rank);
+            int ktot;
+            const int o = pos + block_excl_scan(kp ? 1 : 0, scratch, &ktot);
+            if (kp) {
+                if (o < pend) {
+                    col_out[o] = E.col[q];
+                    const double w = mcl_weight(E.val[q], prm.r);
+                    val_out[o] = wsum > 0.0 ? (float)(w / wsum) : 0.f;
+                } else {
+                    set_status(ctl, ST_INTERNAL);
+                }
+            }
+            pos += ktot;
+        }
+        if (threadIdx.x == 0 && pos != pend) set_status(ctl, ST_INTERNAL);
+        __syncthreads();
+    }
+}
+
+void launch_mcl_step(const spgemm_plan* p, const CsrDev& E, float theta, int k, double r,
+                     int order, const WsPtrs& w, int* rpt_out, int* col_out, float* val_out,
+                     cudaStream_t s) {
+    if (E.rows == 0) {
+        launch_row_ptr(p, w.map, 0, w, rpt_out, s);
+        return;
+    }
+    const MclParams prm{theta, k, r, order};
+    const int sms = p->num_sms;
+    int* counts = w.map;                       // E.rows ints of the workspace
+    SPG_LAUNCH(p, K_MCL, s, k_mcl_warp<false><<<sms * 8, kMclThreads, 0, s>>>(E, prm, counts, nullptr, nullptr, nullptr, w.ctl));
+    SPG_LAUNCH(p, K_MCL, s, k_mcl_block<false><<<sms, kMclBlockThreads, 0, s>>>(E, prm, counts, nullptr, nullptr, nullptr, w.ctl));
+    launch_row_ptr(p, counts, E.rows, w, rpt_out, s);
+    SPG_LAUNCH(p, K_MCL, s, k_mcl_warp<true><<<sms * 8, kMclThreads, 0, s>>>(E, prm, counts, rpt_out, col_out, val_out, w.ctl));
+    SPG_LAUNCH(p, K_MCL, s, k_mcl_block<true><<<sms, kMclBlockThreads, 0, s>>>(E, prm, counts, rpt_out, col_out, val_out, w.ctl));
+}
+
+}  // namespace spg
