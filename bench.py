@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-patterns", action="store_true",
+                    help="skip the batched / served / MCL pattern measurements")
+    ap.add_argument("--gnn-graphs", type=int, default=8192)
+    ap.add_argument("--served-requests", type=int, default=32)
     return ap.parse_args()
 
 
@@ -192,6 +196,180 @@ def tier_work(plan, A_host, ip, nnz):
     return out
 
 
+# ---------------------------------------------------------------------------
+# patterns beside the headline step: batched GNN aggregation (forward graph +
+# backward), served requests (continuous batching vs plain per-request), MCL
+# ---------------------------------------------------------------------------
+
+def _pct(xs, p):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(p * (len(xs) - 1))))] if xs else None
+
+
+def pattern_batched(num_graphs: int, device):
+    """8,192 subgraphs (n log-uniform [64, 2048], degree U[4,32], sym-normalised
+    A_hat, X = per-row top-32 of N(0,1) over 256 features): C = A_hat X as one
+    autotuned, graph-captured product, its backward, and the plain path (one
+    spgemm call per subgraph, all arriving at t = 0)."""
+    import torch
+
+    from paper_2512_12036_gb300 import DeviceCSR, Plan, gen
+    from paper_2512_12036_gb300.batched import autotune, time_graph
+
+    t0 = time.perf_counter()
+    batch = gen.gnn_batch(num_graphs, seed=5)
+    gen_s = time.perf_counter() - t0
+    A = DeviceCSR.from_host(batch.A, device)
+    X = DeviceCSR.from_host(batch.X, device)
+    bs, opts, timings = autotune(A, X, reps=3)
+    ms_fwd = time_graph(bs, reps=5)
+    C = bs.result()
+    ip_total = int(bs.ip_row.sum().item())
+    plan = bs.plan
+    dC = torch.randn(C.nnz, device=device)
+    ws_b = plan.backward_workspace(A, X)
+    plan.backward(A, X, C, dC, ws=ws_b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        plan.backward(A, X, C, dC, ws=ws_b)
+    e1.record()
+    e1.synchronize()
+    ms_bwd = e0.elapsed_time(e1) / 3
+    plan.check_status(ws_b, "batched backward")
+    # plain per-request path over the same subgraphs (all arrive at t = 0)
+    pplan = Plan(device=device.index)
+    off = batch.node_off
+    done_at = []
+    max_rel = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b in range(num_graphs):
+        r0, r1 = int(off[b]), int(off[b + 1])
+        Cb = pplan.spgemm(A.view_rows(r0, r1), X)
+        done_at.append(time.perf_counter() - t0)
+        if b % max(1, num_graphs // 16) == 0:      # same structure and values as the batch
+            s, e = int(C.row_ptr[r0].item()), int(C.row_ptr[r1].item())
+            assert torch.equal(C.col[s:e], Cb.col), "batched and plain structures differ"
+            d = (C.val[s:e] - Cb.val).abs() / Cb.val.abs().clamp_min(1e-30)
+            max_rel = max(max_rel, float(d.max().item()) if d.numel() else 0.0)
+    plain_s = done_at[-1]
+    gflop = 2.0 * ip_total / 1e9
+    return {"workload": f"gnn{num_graphs}_n64-2048_deg4-32_X256_top32", "rows": A.rows,
+            "nnz_A": A.nnz, "nnz_X": X.nnz, "ip": ip_total, "nnz_C": C.nnz,
+            "generate_s": round(gen_s, 1),
+            "batched": {"forward_ms": ms_fwd, "backward_ms": ms_bwd,
+                        "forward_gflops": gflop / (ms_fwd / 1e3),
+                        "p50_ms": ms_fwd, "p99_ms": ms_fwd, "launch": "one CUDA graph replay",
+                        "autotuned_opts": opts, "candidates_ms": timings},
+            "plain": {"total_ms": 1e3 * plain_s, "gflops": gflop / plain_s,
+                      "p50_ms": 1e3 * _pct(done_at, 0.5), "p99_ms": 1e3 * _pct(done_at, 0.99)},
+            "max_rel_diff_batched_vs_plain": max_rel}
+
+
+def pattern_served(n_requests: int, device, A_big=None, S_big=None, St_big=None):
+    """Mixed requests (R-MAT / ER A*B with n log-uniform in [1e3, 1e6] and
+    degree U[4, 32], an MCL expansion M*M, graph contraction S^T A) arriving
+    as a Poisson process at 0.8x the plain path's measured capacity; served
+    by the continuous-batching loop (4 slots, 64 GB budget) vs the plain
+    per-request path on the same arrivals."""
+    import torch
+
+    from paper_2512_12036_gb300 import DeviceCSR, Plan, gen, serving
+
+    rng = np.random.default_rng(6)
+    pool = []
+    for q in range(6):
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
+        d = float(rng.uniform(4, 32))
+        if q % 2:
+            Ah = gen.erdos_renyi(n, d, seed=600 + q)
+            Bh = gen.erdos_renyi(n, d, seed=601 + q)
+        else:
+            sc = int(np.ceil(np.log2(n)))
+            Ah = gen.rmat_symmetric(sc, max(1, int(round(d / 2))), seed=600 + q)
+            Bh = gen.rmat_symmetric(sc, max(1, int(round(d / 2))), seed=601 + q)
+        pool.append((f"{'er' if q % 2 else 'rmat'}_n{Ah.rows}_d{d:.0f}",
+                     DeviceCSR.from_host(Ah, device), DeviceCSR.from_host(Bh, device)))
+    M = gen.rmat_symmetric(16, 8, seed=4, self_loops=True)
+    Md = DeviceCSR.from_host(M, device)
+    from paper_2512_12036_gb300.mcl import normalise_rows
+    Mn = normalise_rows(Plan(device=device.index), Md)
+    pool.append(("mcl_expand_rmat16", Mn, Mn))
+    if St_big is not None:
+        pool.append(("contract_StA_rmat20", St_big, A_big))
+    picks = rng.integers(0, len(pool), size=n_requests)
+
+    def make():
+        return [serving.Request(A=pool[i][1], B=pool[i][2], tag=pool[i][0]) for i in picks]
+
+    # plain capacity: mean service time of the pool, back to back
+    plan = Plan(device=device.index)
+    svc = []
+    for tag, Ad, Bd in pool:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        blocks, ip_t, _ = plan.spgemm_blocks(Ad, Bd)
+        torch.cuda.synchronize()
+        svc.append(time.perf_counter() - t0)
+        del blocks
+    mean_svc = float(np.mean([svc[i] for i in picks]))
+    rate = 0.8 / mean_svc
+    arrivals = serving.poisson_arrivals(n_requests, rate, seed=7)
+    plain = make()
+    t0 = time.perf_counter()
+    for req, at in zip(plain, arrivals):
+        now = time.perf_counter() - t0
+        if now < at:
+            time.sleep(at - now)
+        req.arrival = t0 + at
+        blocks, req.ip, _ = plan.spgemm_blocks(req.A, req.B)
+        torch.cuda.synchronize()
+        del blocks
+        req.done = time.perf_counter()
+    plain_wall = time.perf_counter() - t0
+    srv = serving.gpu_server(slots=4, budget_bytes=64 << 30, device=device.index,
+                             keep_results=False)
+    served = make()
+    t0 = time.perf_counter()
+    serving.run_served(srv, served, arrivals)
+    served_wall = time.perf_counter() - t0
+    srv.close()
+    errs = [r.error for r in served if r.error]
+    gflop = 2.0 * sum(r.ip for r in plain) / 1e9
+    ps, ss = serving.latency_stats(plain), serving.latency_stats(served)
+    return {"requests": n_requests, "pool": [t for t, _, _ in pool],
+            "arrival_rate_per_s": rate, "load": 0.8,
+            "plain": {**ps, "gflops": gflop / plain_wall},
+            "served": {**ss, "gflops": gflop / served_wall, "slots": 4, "budget_gb": 64,
+                       "peak_admitted_gb": srv.adm.peak / 2**30, "errors": len(errs)}}
+
+
+def pattern_mcl(device, iterations: int = 20):
+    """Markov clustering on R-MAT scale 18, edge factor 8, symmetrised, with
+    self-loops: 20 iterations of expansion, prune < 1e-4, top-32, inflation 2,
+    renormalisation."""
+    import torch
+
+    from paper_2512_12036_gb300 import DeviceCSR, Plan, gen
+    from paper_2512_12036_gb300.mcl import markov_cluster
+
+    G = gen.rmat_symmetric(18, 8, seed=4, self_loops=True)
+    Gd = DeviceCSR.from_host(G, device)
+    plan = Plan(device=device.index)
+    markov_cluster(plan, Gd, iterations=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = markov_cluster(plan, Gd, iterations=iterations)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ip = sum(res.ip_history)
+    return {"workload": "rmat18_ef8_selfloops_mcl", "iterations": iterations, "seconds": dt,
+            "expansion_gflops": 2.0 * ip / dt / 1e9, "ip_first": res.ip_history[0],
+            "nnz_final": res.nnz_history[-1]}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -223,6 +401,7 @@ def run_ours(args):
     for ws in (ws_aa, ws_sa, ws_ts):
         plan.check_status(ws, "first pass")
     ip_step = ip_aa + ip_sa + ip_ts
+    n_blocks = len(blocks)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -343,6 +522,17 @@ def run_ours(args):
                "note": "inputs copied from pinned host memory each step; C(S^T A S) and the "
                        "row pointers of every A*A block read back (the A*A values stay in HBM)"}
 
+    patterns = None
+    if rank == 0 and world == 1 and not args.no_patterns:
+        del blocks
+        torch.cuda.empty_cache()
+        patterns = {}
+        patterns["served"] = pattern_served(args.served_requests, dev, A, S, St)
+        torch.cuda.empty_cache()
+        patterns["batched_gnn"] = pattern_batched(args.gnn_graphs, dev)
+        torch.cuda.empty_cache()
+        patterns["mcl"] = pattern_mcl(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(A_h, args.cpu_seconds)
@@ -356,7 +546,7 @@ def run_ours(args):
             "config": {"workload": workload_name(args.scale), "rmat_scale": args.scale,
                        "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05],
                        "nnz_A": A.nnz, "clusters": clusters, "ip_step": ip_step,
-                       "ip_AxA": ip_aa, "nnz_AxA": nnz_aa, "row_blocks_AxA": len(blocks),
+                       "ip_AxA": ip_aa, "nnz_AxA": nnz_aa, "row_blocks_AxA": n_blocks,
                        "nnz_StAS": nnz_ts, "l2": "inputs larger than L2, no flush",
                        "parallelism": f"replicas{world}"},
             "roofline": roof,
@@ -367,6 +557,7 @@ def run_ours(args):
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in
                                    sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "tiers_AxA": {k: {q: v[q] for q in ("rows", "ip", "nnz")} for k, v in work.items()},
+            "patterns": patterns,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

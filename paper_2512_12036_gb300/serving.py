@@ -7,8 +7,10 @@ at most 8*min(IP, rows*cols) bytes plus row pointers, on top of the
 workspace and per-row scratch) and admits it as soon as a slot is free and
 the bound fits the remaining budget. Each slot owns a plan and a CUDA
 stream, so admitted requests overlap on the device while later ones keep
-arriving; a request larger than the whole budget is refused
-(SPGEMM_ERR_BUDGET). Latency is completion minus arrival.
+arriving. A request whose bound exceeds the whole budget is split into
+blocks of consecutive rows that fit (each a zero-copy row view of A) and
+completes when all its blocks have; one that cannot be split small enough
+is refused (SPGEMM_ERR_BUDGET). Latency is completion minus arrival.
 
 The admission logic takes the bound and executor as functions so it can be
 exercised on the CPU with fakes.
@@ -39,6 +41,10 @@ class Request:
     ip: int = 0
     result: object = None
     error: int = 0
+    row_begin: int = 0
+    parent: object = None
+    parts: list = None
+    pending: int = 0
     event: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -75,8 +81,9 @@ class Server:
     """Dispatcher + slot workers. ``bound_fn(req) -> (bytes, ip)`` and
     ``exec_fn(slot, req) -> result`` do the device work (see gpu_server)."""
 
-    def __init__(self, bound_fn, exec_fn, slots: int = 4, budget_bytes: int = 64 << 30):
-        self.bound_fn, self.exec_fn = bound_fn, exec_fn
+    def __init__(self, bound_fn, exec_fn, slots: int = 4, budget_bytes: int = 64 << 30,
+                 split_fn=None):
+        self.bound_fn, self.exec_fn, self.split_fn = bound_fn, exec_fn, split_fn
         self.adm = Admission(budget_bytes, slots)
         self.inbox: queue.Queue = queue.Queue()
         self.slot_q = [queue.Queue() for _ in range(slots)]
@@ -106,14 +113,24 @@ class Server:
                     q.put(None)
                 return
             req.bound, req.ip = self.bound_fn(req)
+            parts = [req]
             if req.bound > self.adm.budget:
-                req.error = ERR_BUDGET
-                req.done = time.perf_counter()
-                req.event.set()
-                continue
-            slot = self.adm.acquire(req.bound)
-            req.admitted = time.perf_counter()
-            self.slot_q[slot].put(req)
+                parts = self.split_fn(req, self.adm.budget) if self.split_fn else None
+                if not parts or any(p.bound > self.adm.budget for p in parts):
+                    req.error = ERR_BUDGET
+                    req.done = time.perf_counter()
+                    req.event.set()
+                    continue
+                req.parts = parts
+                req.pending = len(parts)
+                for p in parts:
+                    p.parent = req
+            for p in parts:
+                slot = self.adm.acquire(p.bound)
+                p.admitted = time.perf_counter()
+                if p is not req and not req.admitted:
+                    req.admitted = p.admitted
+                self.slot_q[slot].put(p)
 
     def _work(self, slot: int) -> None:
         while True:
@@ -126,7 +143,19 @@ class Server:
                 req.error = getattr(exc, "code", -1)
             req.done = time.perf_counter()
             self.adm.release(slot, req.bound)
-            req.event.set()
+            parent = req.parent
+            if parent is None:
+                req.event.set()
+                continue
+            with self._lock:
+                parent.pending -= 1
+                if req.error:
+                    parent.error = req.error
+                last = parent.pending == 0
+            if last:
+                parent.result = [p.result for p in parent.parts]
+                parent.done = time.perf_counter()
+                parent.event.set()
 
     def close(self) -> None:
         self.inbox.put(None)
@@ -155,8 +184,10 @@ def request_bound(plan, A, B, ws, ip_total: int) -> int:
 
 
 def gpu_server(slots: int = 4, budget_bytes: int = 64 << 30, device: int = 0,
-               max_block_nnz: int = 2**31 - 1) -> Server:
-    """A Server whose slots each own a Plan and a CUDA stream."""
+               max_block_nnz: int = 2**31 - 1, keep_results: bool = True) -> Server:
+    """A Server whose slots each own a Plan and a CUDA stream. With
+    keep_results=False a request's result is consumed on completion: only
+    (rows, nnz, sum of values) is kept and C's memory returns to the pool."""
     import torch
 
     from .api import Plan
@@ -171,8 +202,32 @@ def gpu_server(slots: int = 4, budget_bytes: int = 64 << 30, device: int = 0,
         torch.cuda.set_device(device)
         with torch.cuda.stream(count_stream):
             ws = count_plan.workspace(req.A, req.B)
-            _, ip_total = count_plan.count(req.A, req.B, ws)
+            ip_row, ip_total = count_plan.count(req.A, req.B, ws)
+        req.ip_row = ip_row
         return request_bound(count_plan, req.A, req.B, ws, ip_total), ip_total
+
+    def split_fn(req, budget):
+        """Blocks of consecutive rows whose bounds fit half the budget."""
+        ip = req.ip_row.cpu().numpy()
+        cols = int(req.B.cols)
+        csum = np.cumsum(np.minimum(ip, cols) * 8 + 16)
+        target = budget // 2
+        parts, r0, base = [], 0, 0
+        while r0 < ip.size:
+            r1 = max(int(np.searchsorted(csum, base + target, side="right")), r0 + 1)
+            parts.append((r0, r1))
+            base = int(csum[r1 - 1])
+            r0 = r1
+        out = []
+        for a, b in parts:
+            sub = Request(A=req.A.view_rows(a, b), B=req.B, tag=req.tag, row_begin=a)
+            sub.arrival = req.arrival
+            with torch.cuda.stream(count_stream):
+                ws = count_plan.workspace(sub.A, sub.B)
+                _, ipt = count_plan.count(sub.A, sub.B, ws)
+            sub.bound, sub.ip = request_bound(count_plan, sub.A, sub.B, ws, ipt), ipt
+            out.append(sub)
+        return out
 
     def exec_fn(slot, req):
         torch.cuda.set_device(device)
@@ -180,11 +235,14 @@ def gpu_server(slots: int = 4, budget_bytes: int = 64 << 30, device: int = 0,
         with torch.cuda.stream(streams[slot]):
             ws = plan.workspace(req.A, req.B)
             blocks, _, _ = plan.spgemm_blocks(req.A, req.B, max_block_nnz=max_block_nnz, ws=ws)
+            if not keep_results:
+                summary = (req.A.rows, sum(C.nnz for _, _, C in blocks),
+                           float(sum(C.val.double().sum() for _, _, C in blocks)))
             streams[slot].synchronize()
             plan.check_status(ws, "served request")
-        return blocks
+        return blocks if keep_results else summary
 
-    return Server(bound_fn, exec_fn, slots, budget_bytes)
+    return Server(bound_fn, exec_fn, slots, budget_bytes, split_fn=split_fn)
 
 
 def run_plain(reqs, arrivals, device: int = 0, max_block_nnz: int = 2**31 - 1):

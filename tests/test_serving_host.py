@@ -67,3 +67,25 @@ def test_latency_stats_and_arrivals():
     assert st["n"] == 100 and abs(st["p50_ms"] - 50.5) < 1.0 and st["p99_ms"] >= 98.0
     arr = serving.poisson_arrivals(20000, rate=100.0, seed=1)
     assert abs(arr[-1] / 20000 - 0.01) < 0.001 and (arr > 0).all()
+
+
+def test_oversize_request_split_into_parts():
+    def split_fn(req, budget):
+        parts = []
+        for q in range(4):
+            p = serving.Request(A=req.A // 4, B=q)
+            p.bound = req.A // 4
+            parts.append(p)
+        return parts
+
+    srv = serving.Server(lambda r: (r.A, 0), lambda slot, r: (r.B, r.A), slots=2,
+                         budget_bytes=50, split_fn=split_fn)
+    big = srv.submit(serving.Request(A=160, B=None))
+    small = srv.submit(serving.Request(A=10, B=None))
+    huge = srv.submit(serving.Request(A=1000, B=None))
+    for r in (big, small, huge):
+        assert r.event.wait(5)
+    srv.close()
+    assert big.error == 0 and sorted(big.result) == [(q, 40) for q in range(4)]
+    assert small.error == 0 and huge.error == ERR_BUDGET
+    assert srv.adm.peak <= 50
