@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-patterns", action="store_true",
                     help="skip the batched / served / MCL pattern measurements")
     ap.add_argument("--gnn-graphs", type=int, default=8192)
+    ap.add_argument("--panel-cols", type=int, default=None)
     ap.add_argument("--served-requests", type=int, default=32)
     return ap.parse_args()
 
@@ -388,7 +389,10 @@ def run_ours(args):
     A = DeviceCSR.from_host(A_h, dev)
     S = DeviceCSR.from_host(S_h, dev)
     St = DeviceCSR.from_host(St_h, dev)
-    plan = Plan(device=local)
+    opts = {}
+    if args.panel_cols:
+        opts["panel_cols"] = args.panel_cols
+    plan = Plan(device=local, **opts)
     ws_aa = plan.workspace(A, A)
     ws_sa = plan.workspace(St, A)
 
@@ -548,6 +552,7 @@ def run_ours(args):
                        "nnz_A": A.nnz, "clusters": clusters, "ip_step": ip_step,
                        "ip_AxA": ip_aa, "nnz_AxA": nnz_aa, "row_blocks_AxA": n_blocks,
                        "nnz_StAS": nnz_ts, "l2": "inputs larger than L2, no flush",
+                       "plan_opts": plan.opts,
                        "parallelism": f"replicas{world}"},
             "roofline": roof,
             "step_hbm_fraction": {"compulsory_bytes_AxA": int(compulsory), "frac": step_frac,
