@@ -336,7 +336,22 @@ def pattern_served(n_requests: int, device, A_big=None, S_big=None, St_big=None)
     t0 = time.perf_counter()
     serving.run_served(srv, served, arrivals)
     served_wall = time.perf_counter() - t0
+    # saturation: the same requests all arriving at once (maximum throughput)
+    burst_served = make()
+    t0 = time.perf_counter()
+    serving.run_served(srv, burst_served, np.zeros(n_requests))
+    burst_served_wall = time.perf_counter() - t0
     srv.close()
+    burst_plain = make()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for req in burst_plain:
+        req.arrival = t0
+        blocks, req.ip, _ = plan.spgemm_blocks(req.A, req.B)
+        torch.cuda.synchronize()
+        del blocks
+        req.done = time.perf_counter()
+    burst_plain_wall = time.perf_counter() - t0
     errs = [r.error for r in served if r.error]
     gflop = 2.0 * sum(r.ip for r in plain) / 1e9
     ps, ss = serving.latency_stats(plain), serving.latency_stats(served)
@@ -344,7 +359,11 @@ def pattern_served(n_requests: int, device, A_big=None, S_big=None, St_big=None)
             "arrival_rate_per_s": rate, "load": 0.8,
             "plain": {**ps, "gflops": gflop / plain_wall},
             "served": {**ss, "gflops": gflop / served_wall, "slots": 4, "budget_gb": 64,
-                       "peak_admitted_gb": srv.adm.peak / 2**30, "errors": len(errs)}}
+                       "peak_admitted_gb": srv.adm.peak / 2**30, "errors": len(errs)},
+            "burst_plain": {**serving.latency_stats(burst_plain),
+                            "gflops": gflop / burst_plain_wall},
+            "burst_served": {**serving.latency_stats(burst_served),
+                             "gflops": gflop / burst_served_wall}}
 
 
 def pattern_mcl(device, iterations: int = 20):

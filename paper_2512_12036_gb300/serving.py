@@ -7,10 +7,12 @@ at most 8*min(IP, rows*cols) bytes plus row pointers, on top of the
 workspace and per-row scratch) and admits it as soon as a slot is free and
 the bound fits the remaining budget. Each slot owns a plan and a CUDA
 stream, so admitted requests overlap on the device while later ones keep
-arriving. A request whose bound exceeds the whole budget is split into
+arriving. A request whose bound exceeds a slot's share is split into
 blocks of consecutive rows that fit (each a zero-copy row view of A) and
 completes when all its blocks have; one that cannot be split small enough
-is refused (SPGEMM_ERR_BUDGET). Latency is completion minus arrival.
+is refused (SPGEMM_ERR_BUDGET). The GPU back end preallocates every slot's
+share once, so serving itself allocates no device memory. Latency is
+completion minus arrival.
 
 The admission logic takes the bound and executor as functions so it can be
 exercised on the CPU with fakes.
@@ -82,9 +84,10 @@ class Server:
     ``exec_fn(slot, req) -> result`` do the device work (see gpu_server)."""
 
     def __init__(self, bound_fn, exec_fn, slots: int = 4, budget_bytes: int = 64 << 30,
-                 split_fn=None):
+                 split_fn=None, request_limit: int | None = None):
         self.bound_fn, self.exec_fn, self.split_fn = bound_fn, exec_fn, split_fn
         self.adm = Admission(budget_bytes, slots)
+        self.limit = int(request_limit) if request_limit is not None else int(budget_bytes)
         self.inbox: queue.Queue = queue.Queue()
         self.slot_q = [queue.Queue() for _ in range(slots)]
         self.requests: list[Request] = []
@@ -114,9 +117,9 @@ class Server:
                 return
             req.bound, req.ip = self.bound_fn(req)
             parts = [req]
-            if req.bound > self.adm.budget:
-                parts = self.split_fn(req, self.adm.budget) if self.split_fn else None
-                if not parts or any(p.bound > self.adm.budget for p in parts):
+            if req.bound > self.limit:
+                parts = self.split_fn(req, self.limit) if self.split_fn else None
+                if not parts or any(p.bound > self.limit for p in parts):
                     req.error = ERR_BUDGET
                     req.done = time.perf_counter()
                     req.event.set()
@@ -176,38 +179,79 @@ def latency_stats(reqs) -> dict:
 # GPU back end
 # ---------------------------------------------------------------------------
 
-def request_bound(plan, A, B, ws, ip_total: int) -> int:
+def request_bound(plan, A, B, ws_bytes: int, ip_total: int) -> int:
     """Device bytes a request may need: workspace, IP/nnz scratch, row
-    pointers and C (nnz(C) <= min(IP, rows*cols))."""
+    pointers and C (nnz(C) <= min(IP, rows*cols)), with alignment slack."""
     nnz_bound = min(int(ip_total), int(A.rows) * int(B.cols))
-    return (int(ws.numel()) + 12 * A.rows + 4 * (A.rows + 1) + 8 * nnz_bound)
+    return (int(ws_bytes) + 12 * A.rows + 4 * (A.rows + 1) + 8 * nnz_bound + 8 * 256)
+
+
+class Arena:
+    """Views carved from one preallocated device buffer (no allocation while
+    serving); every view starts on a 256-byte boundary."""
+
+    def __init__(self, nbytes: int, device):
+        import torch
+        self.buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
+        self.base = (-self.buf.data_ptr()) % 256
+        self.nbytes = int(nbytes)
+        self.off = 0
+
+    def reset(self) -> None:
+        self.off = 0
+
+    def take(self, nbytes: int, dtype):
+        import torch
+        nbytes = int(nbytes)
+        start = self.base + self.off
+        self.off += (nbytes + 255) // 256 * 256
+        if self.off > self.nbytes:
+            raise MemoryError("arena exhausted")
+        view = self.buf[start:start + nbytes]
+        return view.view(dtype) if dtype is not torch.uint8 else view
+
+    def free(self) -> int:
+        return self.nbytes - self.off
 
 
 def gpu_server(slots: int = 4, budget_bytes: int = 64 << 30, device: int = 0,
-               max_block_nnz: int = 2**31 - 1, keep_results: bool = True) -> Server:
-    """A Server whose slots each own a Plan and a CUDA stream. With
-    keep_results=False a request's result is consumed on completion: only
-    (rows, nnz, sum of values) is kept and C's memory returns to the pool."""
+               keep_results: bool = True, count_ws_bytes: int = 1 << 30,
+               max_rows: int = 1 << 22) -> Server:
+    """A Server whose slots each own a Plan, a CUDA stream and an arena of
+    budget_bytes / slots preallocated device memory holding the request's
+    workspace, per-row scratch and C, so serving allocates nothing. A
+    request is admitted when a slot is free and its bound fits an arena;
+    larger ones are split into row blocks that do. With keep_results=False
+    a result is consumed on completion ((rows, nnz) is kept); otherwise C is
+    copied out of the arena into its own tensors."""
     import torch
 
-    from .api import Plan
+    from .api import DeviceCSR, Plan
 
     torch.cuda.set_device(device)
+    dev = torch.device("cuda", device)
+    per_slot = int(budget_bytes) // slots
     plans = [Plan(device=device) for _ in range(slots)]
     streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+    arenas = [Arena(per_slot, dev) for _ in range(slots)]
     count_plan = Plan(device=device)
     count_stream = torch.cuda.Stream(device=device)
+    count_arena = Arena(count_ws_bytes + 8 * max_rows, dev)
 
     def bound_fn(req):
         torch.cuda.set_device(device)
+        count_arena.reset()
+        nws = count_plan.workspace_bytes(req.A, req.B)
         with torch.cuda.stream(count_stream):
-            ws = count_plan.workspace(req.A, req.B)
-            ip_row, ip_total = count_plan.count(req.A, req.B, ws)
-        req.ip_row = ip_row
-        return request_bound(count_plan, req.A, req.B, ws, ip_total), ip_total
+            ws = count_arena.take(nws, torch.uint8)
+            count_plan.workspace_init(ws)
+            ip_row = count_arena.take(8 * max(req.A.rows, 1), torch.int64)[:req.A.rows]
+            ip_row, ip_total = count_plan.count(req.A, req.B, ws, ip_row=ip_row)
+        req.ip_row = ip_row.clone() if req.A.rows else ip_row
+        return request_bound(count_plan, req.A, req.B, nws, ip_total), ip_total
 
     def split_fn(req, budget):
-        """Blocks of consecutive rows whose bounds fit half the budget."""
+        """Blocks of consecutive rows whose bounds fit half an arena."""
         ip = req.ip_row.cpu().numpy()
         cols = int(req.B.cols)
         csum = np.cumsum(np.minimum(ip, cols) * 8 + 16)
@@ -222,27 +266,39 @@ def gpu_server(slots: int = 4, budget_bytes: int = 64 << 30, device: int = 0,
         for a, b in parts:
             sub = Request(A=req.A.view_rows(a, b), B=req.B, tag=req.tag, row_begin=a)
             sub.arrival = req.arrival
-            with torch.cuda.stream(count_stream):
-                ws = count_plan.workspace(sub.A, sub.B)
-                _, ipt = count_plan.count(sub.A, sub.B, ws)
-            sub.bound, sub.ip = request_bound(count_plan, sub.A, sub.B, ws, ipt), ipt
+            nws = count_plan.workspace_bytes(sub.A, sub.B)
+            sub.ip = int(ip[a:b].sum())
+            sub.bound = request_bound(count_plan, sub.A, sub.B, nws, sub.ip)
             out.append(sub)
         return out
 
     def exec_fn(slot, req):
         torch.cuda.set_device(device)
-        plan = plans[slot]
-        with torch.cuda.stream(streams[slot]):
-            ws = plan.workspace(req.A, req.B)
-            blocks, _, _ = plan.spgemm_blocks(req.A, req.B, max_block_nnz=max_block_nnz, ws=ws)
-            if not keep_results:
-                summary = (req.A.rows, sum(C.nnz for _, _, C in blocks),
-                           float(sum(C.val.double().sum() for _, _, C in blocks)))
-            streams[slot].synchronize()
-            plan.check_status(ws, "served request")
-        return blocks if keep_results else summary
+        plan, ar, st = plans[slot], arenas[slot], streams[slot]
+        ar.reset()
+        A, B = req.A, req.B
+        with torch.cuda.stream(st):
+            ws = ar.take(plan.workspace_bytes(A, B), torch.uint8)
+            plan.workspace_init(ws)
+            ip_row = ar.take(8 * max(A.rows, 1), torch.int64)[:A.rows]
+            row_nnz = ar.take(4 * max(A.rows, 1), torch.int32)[:A.rows]
+            row_ptr = ar.take(4 * (A.rows + 1), torch.int32)
+            plan.count(A, B, ws, ip_row=ip_row, total=False)
+            _, nnz = plan.symbolic(A, B, ip_row, ws, row_nnz=row_nnz)
+            cap = ar.free() // 8 - 64
+            if nnz > cap or nnz > 2**31 - 1:
+                raise MemoryError("request exceeds its arena")
+            col = ar.take(4 * max(nnz, 1), torch.int32)[:nnz]
+            val = ar.take(4 * max(nnz, 1), torch.float32)[:nnz]
+            plan.row_ptr(row_nnz, ws, out=row_ptr)
+            plan.numeric(A, B, ip_row, row_ptr, ws, col, val)
+            if keep_results:
+                C = DeviceCSR(A.rows, B.cols, row_ptr.clone(), col.clone(), val.clone())
+            st.synchronize()
+            plan.check_status(ws, "served request", stream=st)
+        return C if keep_results else (A.rows, nnz)
 
-    return Server(bound_fn, exec_fn, slots, budget_bytes, split_fn=split_fn)
+    return Server(bound_fn, exec_fn, slots, budget_bytes, split_fn=split_fn, request_limit=per_slot)
 
 
 def run_plain(reqs, arrivals, device: int = 0, max_block_nnz: int = 2**31 - 1):

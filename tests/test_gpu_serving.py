@@ -49,7 +49,7 @@ def test_results_same_alone_and_in_the_mix():
         assert rm.error == 0, t
         ref = oracle.spgemm(Ah, Bh)
         (_, _, Ca), = ra.result
-        (_, _, Cm), = rm.result
+        Cm = rm.result
         ha, hm = Ca.to_host(), Cm.to_host()
         assert np.array_equal(ha.row_ptr, hm.row_ptr) and np.array_equal(ha.col, hm.col), t
         compare(ha, ref)
