@@ -10,11 +10,13 @@ void occupancy_numeric(spgemm_plan* p);
 void occupancy_backward(spgemm_plan* p);
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long long b_cols) {
+WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long long b_cols,
+                   long long b_nnz) {
     WsLayout L;
     L.m = (int)m;
     L.nblk = (int)((m + kBinRows - 1) / kBinRows);
-    L.nscan = (int)((m + kScanItems - 1) / kScanItems);
+    const long long nscan_rows = m > b_cols ? m : b_cols;
+    L.nscan = (int)((nscan_rows + kScanItems - 1) / kScanItems);
     const long long pw = p->opts.panel_cols;
     L.panels = (int)((b_cols + pw - 1) / pw);
     size_t off = 0;
@@ -29,6 +31,17 @@ WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long lon
     L.bpanel = off;
     if (L.panels > 0 && L.panels <= kMaxPanels && b_rows > 0)
         off = align256(off + sizeof(int) * (size_t)b_rows * (size_t)(L.panels + 1));
+    if (b_cols > 0 && b_nnz > 0) {
+        L.has_hot = true;
+        L.colcnt = off;
+        off = align256(off + sizeof(int) * (size_t)(b_cols + 1));
+        L.hot_rank = off;
+        off = align256(off + sizeof(int) * (size_t)(b_cols + 1));
+        L.hot_col = off;
+        off = align256(off + sizeof(int) * (size_t)b_cols);
+        L.bhot = off;
+        off = align256(off + sizeof(int) * (size_t)b_nnz);
+    }
     L.total = off;
     return L;
 }
@@ -40,7 +53,12 @@ WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols) {
     w.map = (int*)(b + L.map);
     w.blk_counts = (int*)(b + L.blk_counts);
     w.scan_part = (long long*)(b + L.scan_part);
-    w.bpanel = L.total > L.bpanel ? (int*)(b + L.bpanel) : nullptr;
+    w.bpanel = (L.panels > 0 && L.panels <= kMaxPanels && (L.has_hot ? L.colcnt : L.total) > L.bpanel)
+                   ? (int*)(b + L.bpanel) : nullptr;
+    w.colcnt = L.has_hot ? (int*)(b + L.colcnt) : nullptr;
+    w.hot_rank = L.has_hot ? (int*)(b + L.hot_rank) : nullptr;
+    w.hot_col = L.has_hot ? (int*)(b + L.hot_col) : nullptr;
+    w.bhot = L.has_hot ? (int*)(b + L.bhot) : nullptr;
     w.nblk = L.nblk;
     w.nscan = L.nscan;
     w.panels = L.panels;
@@ -58,7 +76,7 @@ const char* const kKernelNames[K_NUM_KERNELS] = {
     "fill", "check_rpt", "zero_total", "ip_count", "sum", "group_hist", "group_scan",
     "group_scatter", "scan_part", "scan_top", "scan_final", "reset_flag", "bpanel", "sym_esc",
     "sym_warp", "sym_block", "sym_dense", "num_esc", "num_warp32", "num_warp64", "num_block32",
-    "num_block64", "num_dense32", "num_dense64", "backward", "guard", "mcl"};
+    "num_block64", "num_dense32", "num_dense64", "backward", "guard", "mcl", "hot"};
 
 void prof_begin(const spgemm_plan* p, int kid, cudaStream_t s) {
     (void)kid;
@@ -128,7 +146,7 @@ static int check_pair(const spgemm_plan* plan, const spgemm_csr* A, const spgemm
 
 static int check_ws(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, void* ws,
                     size_t ws_bytes, WsLayout* L) {
-    *L = ws_layout(plan, A->rows, B->rows, B->cols);
+    *L = ws_layout(plan, A->rows, B->rows, B->cols, B->nnz);
     if (!ws || ws_bytes < L->total) return SPGEMM_ERR_WORKSPACE;
     if (((uintptr_t)ws & 255) != 0) return SPGEMM_ERR_WORKSPACE;
     return SPGEMM_OK;
@@ -301,7 +319,7 @@ int spgemm_workspace_bytes(const spgemm_plan* plan, const spgemm_csr* A, const s
                            size_t* bytes) {
     if (!plan || !A || !B || !bytes) return SPGEMM_ERR_INVALID;
     if (A->rows < 0 || B->rows < 0 || B->cols < 0) return SPGEMM_ERR_INVALID;
-    *bytes = ws_layout(plan, A->rows, B->rows, B->cols).total;
+    *bytes = ws_layout(plan, A->rows, B->rows, B->cols, B->nnz).total;
     return SPGEMM_OK;
 }
 
@@ -362,6 +380,7 @@ int spgemm_symbolic(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_c
     CsrDev dA = dev_view(A), dB = dev_view(B);
     launch_symbolic(plan, dA, dB, (const long long*)ip_row, w, row_nnz, s);
     launch_bpanel(plan, dB, w, s);
+    launch_hot(plan, dB, w, s);
     launch_nnz_total(plan, row_nnz, A->rows, w, s);
     rc = cuda_err(cudaGetLastError());
     if (rc) return rc;
@@ -424,7 +443,7 @@ int spgemm(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_csr* B, vo
     if (total > 0 && (!col || !val)) return SPGEMM_ERR_BUDGET;
     rc = spgemm_numeric(plan, A, B, ip_row, 0, A->rows, row_ptr_C, ws, ws_bytes, col, val, stream);
     if (rc) return rc;
-    WsLayout L = ws_layout(plan, A->rows, B->rows, B->cols);
+    WsLayout L = ws_layout(plan, A->rows, B->rows, B->cols, B->nnz);
     return sync_read(ws_ptrs(L, ws, plan->opts.panel_cols).ctl, -1, nullptr, (cudaStream_t)stream);
 }
 
@@ -446,6 +465,7 @@ int spgemm_batched(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_cs
     launch_ip_count(plan, dA, dB, (long long*)ip_row, w, s);
     launch_symbolic(plan, dA, dB, (const long long*)ip_row, w, row_nnz, s);
     launch_bpanel(plan, dB, w, s);
+    launch_hot(plan, dB, w, s);
     launch_row_ptr(plan, row_nnz, A->rows, w, row_ptr_C, s);
     launch_copy_total(plan, w, 2, (long long*)nnz_C, s);
     launch_numeric(plan, dA, dB, (const long long*)ip_row, 0, A->rows, row_ptr_C, w, col_C, val_C,

@@ -14,7 +14,7 @@ enum KernelId : int {
     K_FILL, K_CHECK_RPT, K_ZERO, K_IP_COUNT, K_SUM, K_GROUP_HIST, K_GROUP_SCAN, K_GROUP_SCATTER,
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_FINAL, K_RESET, K_BPANEL, K_SYM_ESC, K_SYM_WARP, K_SYM_BLOCK,
     K_SYM_DENSE, K_NUM_ESC, K_NUM_WARP32, K_NUM_WARP64, K_NUM_BLOCK32, K_NUM_BLOCK64,
-    K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_GUARD, K_MCL, K_NUM_KERNELS
+    K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_GUARD, K_MCL, K_HOT, K_NUM_KERNELS
 };
 extern const char* const kKernelNames[K_NUM_KERNELS];
 
@@ -37,7 +37,7 @@ struct spgemm_plan {
     // resident blocks per SM for each persistent kernel (filled at creation)
     int occ_sym_warp, occ_sym_block, occ_sym_dense;
     int occ_num_warp32, occ_num_warp64, occ_num_block32, occ_num_block64;
-    int occ_num_dense32, occ_num_dense64;
+    int occ_num_dense32, occ_num_dense64, occ_num_dense_hot;
 };
 
 namespace spg {
@@ -81,11 +81,17 @@ struct WsLayout {
     size_t blk_counts = 0;   // int32 [kNumBins][nblk]
     size_t scan_part = 0;    // int64 [nscan + 1]
     size_t bpanel = 0;       // int32 [B.rows][P+1]  (0 bytes when P > kMaxPanels)
+    size_t colcnt = 0;       // int32 [B.cols+1]  entries per column of B, then hot flags
+    size_t hot_rank = 0;     // int32 [B.cols+1]  exclusive prefix of the hot flags
+    size_t hot_col = 0;      // int32 [B.cols]    hot columns in ascending order
+    size_t bhot = 0;         // int32 [B.nnz]     hot rank of each B entry's column, or -1
+    bool has_hot = false;
     size_t total = 0;
     int m = 0, nblk = 0, nscan = 0, panels = 0;
 };
 
-WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long long b_cols);
+WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long long b_cols,
+                   long long b_nnz = 0);
 
 struct WsPtrs {
     Ctl* ctl;
@@ -93,6 +99,10 @@ struct WsPtrs {
     int* blk_counts;
     long long* scan_part;
     int* bpanel;
+    int* colcnt;
+    int* hot_rank;
+    int* hot_col;
+    int* bhot;
     int nblk, nscan, panels, panel_cols;
 };
 
@@ -133,6 +143,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                     int row_begin, int row_end, const int* rptC, const WsPtrs& w, int* colC,
                     float* valC, cudaStream_t s, long long capacity = -1);
 void launch_bpanel(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaStream_t s);
+void launch_hot(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaStream_t s);
 void launch_copy_total(const spgemm_plan* p, const WsPtrs& w, int which, long long* dst,
                        cudaStream_t s);
 

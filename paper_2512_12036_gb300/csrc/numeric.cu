@@ -530,6 +530,196 @@ __global__ void __launch_bounds__(kNumDenseThreads, 1) k_num_dense(CsrDev A, Csr
     }
 }
 
+// Heavy rows whose entries can gather more than fp32_max_terms products
+// (the fp64 tier). Products on cold columns of B (see hot.cu) are summed in
+// fp32 exactly as in the fp32 tier; products on hot columns go to per-warp
+// private fp64 partial sums in shared memory (one slot per hot column of the
+// pass), which keeps the fp64 atomics free of cross-warp contention on the
+// hub columns that R-MAT rows all share. After a pass the warps' partials
+// are added (fp64), rounded once into the pass array and emitted with the
+// cold columns in column order. A pass covers one table panel; when a panel
+// holds more hot columns than there are slots it is split into sub-passes
+// at hot-column boundaries (re-reading the panel's segments).
+constexpr int kHotSlots = 512;
+constexpr int kHotThreads = 1024;
+constexpr int kHotWarps = kHotThreads / 32;
+
+struct KeyValHot {
+    int key;
+    float v;
+    int hot;
+};
+
+__global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrDev B,
+                                                                  const int* map, Ctl* ctl,
+                                                                  const int* rptC, int row_begin,
+                                                                  int* colC, float* valC,
+                                                                  int bin_lo, int bin_hi, int tier,
+                                                                  const int* tab, int P, int PW,
+                                                                  const int* hot_rank,
+                                                                  const int* hot_col,
+                                                                  const int* bhot) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double* priv = reinterpret_cast<double*>(sm_raw);                 // [kHotWarps][kHotSlots]
+    float* st = reinterpret_cast<float*>(sm_raw + sizeof(double) * kHotWarps * kHotSlots);
+    unsigned* bm = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(st) +
+                                               sizeof(float) * PW);
+    __shared__ int s_idx;
+    __shared__ int scratch[33];
+    __shared__ ExpandTile<kHotThreads, float> tile;
+    const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
+    if (begin >= end) return;
+    const int t = threadIdx.x, warp = t >> 5;
+    const int nwords = PW >> 5;
+    for (int i = t; i < PW; i += kHotThreads) st[i] = 0.f;
+    for (int i = t; i < nwords; i += kHotThreads) bm[i] = 0u;
+    for (int i = t; i < kHotWarps * kHotSlots; i += kHotThreads) priv[i] = 0.0;
+    const bool use_tab = tab != nullptr && ctl->b_unsorted == 0;
+    const int npass = P;                                  // one table panel per pass
+    const long long stride = P + 1;
+    double* mypriv = priv + warp * kHotSlots;
+
+    int pc0 = 0, lo = 0, hi = 0, hr0 = 0;                 // panel start, sub-pass [lo, hi)
+    auto load = [&](int q) { return KeyValHot{B.col[q], B.val[q], bhot[q]}; };
+    auto apply = [&](KeyValHot kv, float a) {
+        if (!key_in(kv.key, B, ctl)) return;
+        if (kv.key < lo || kv.key >= hi) {
+            if (use_tab && (kv.key < pc0 || kv.key >= pc0 + PW)) set_status(ctl, ST_INTERNAL);
+            return;
+        }
+        const int kk = kv.key - pc0;
+        atomicOr(&bm[kk >> 5], 1u << (kk & 31));
+        if (kv.hot >= 0) {
+            const int slot = kv.hot - hr0;
+            if ((unsigned)slot < (unsigned)kHotSlots)
+                atomicAdd(&mypriv[slot], (double)a * (double)kv.v);
+            else
+                set_status(ctl, ST_INTERNAL);
+        } else {
+            atomicAdd(&st[kk], a * kv.v);
+        }
+    };
+
+    for (;;) {
+        if (t == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= end) break;
+        const int r = map[idx];
+        const int row = row_begin + r;
+        const int out = rptC[r];
+        const int nnz_row = rptC[r + 1] - out;
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        const int na = re - rs;
+        const bool cached = use_tab && na <= kHotThreads;
+        int myk = -1, cur = 0, nxt = 0;
+        float mya = 0.f;
+        if (cached && t < na) {
+            const int j = rs + t;
+            const int k = A.col[j];
+            if ((unsigned)k < (unsigned)B.rows) {
+                myk = k;
+                mya = A.val[j];
+                cur = tab[(long long)k * stride];
+                nxt = tab[(long long)k * stride + (P > 0 ? 1 : 0)];
+            } else {
+                set_status(ctl, ST_INVALID);
+            }
+        }
+        int written = 0;
+        for (int pass = 0; pass < npass; ++pass) {
+            pc0 = pass * PW;
+            const int pc1 = (int)(B.cols - (long long)pc0 < PW ? B.cols : pc0 + PW);
+            int nxt2 = 0;
+            if (cached && myk >= 0 && pass + 1 < npass)
+                nxt2 = tab[(long long)myk * stride + pass + 2];
+            int bs = 0, len = 0;
+            if (cached && myk >= 0) {
+                if (cur < 0 || nxt < cur || (long long)nxt > B.nnz) set_status(ctl, ST_INTERNAL);
+                else {
+                    bs = cur;
+                    len = nxt - cur;
+                }
+            }
+            // sub-passes of at most kHotSlots hot columns
+            for (lo = pc0; lo < pc1; lo = hi) {
+                hr0 = hot_rank[lo];
+                const int hr_end = hot_rank[pc1];
+                hi = hr_end - hr0 <= kHotSlots ? pc1 : hot_col[hr0 + kHotSlots];
+                if (hi <= lo || hi > pc1) {              // defensive: malformed hot data
+                    set_status(ctl, ST_INTERNAL);
+                    hi = pc1;
+                }
+                if (cached) {
+                    expand_tile<kHotThreads, float, 4>(tile, bs, len, mya, load, apply);
+                } else {
+                    for (int tb = rs; tb < re; tb += kHotThreads) {
+                        const int j = tb + t;
+                        int tbs = 0, tlen = 0;
+                        float a = 0.f;
+                        if (j < re) {
+                            a_entry(A, B, j, tbs, tlen, ctl);
+                            a = A.val[j];
+                            if (use_tab && tlen > 0) {
+                                const int* tk = tab + (long long)A.col[j] * stride;
+                                const int ps = tk[pass], pe = tk[pass + 1];
+                                if (ps >= tbs && pe >= ps && pe <= tbs + tlen) {
+                                    tbs = ps;
+                                    tlen = pe - ps;
+                                } else {
+                                    set_status(ctl, ST_INTERNAL);
+                                    tlen = 0;
+                                }
+                            }
+                        }
+                        expand_tile<kHotThreads, float, 4>(tile, tbs, tlen, a, load, apply);
+                    }
+                }
+                // fold the warps' fp64 partials of the hot columns into the pass array
+                const int nh = (hot_rank[hi] - hr0);
+                for (int h = t; h < nh; h += kHotThreads) {
+                    double v = 0.0;
+                    for (int w2 = 0; w2 < kHotWarps; ++w2) {
+                        v += priv[w2 * kHotSlots + h];
+                        priv[w2 * kHotSlots + h] = 0.0;
+                    }
+                    const int kk = hot_col[hr0 + h] - pc0;
+                    if ((unsigned)kk < (unsigned)PW) st[kk] = (float)v;
+                }
+                __syncthreads();
+                // emit [lo, hi) in column order (bits outside it are clear)
+                const int w0 = (lo - pc0) >> 5;
+                const int w1 = (hi - pc0 + 31) >> 5;
+                const unsigned word = (w0 + t < w1) ? bm[w0 + t] : 0u;
+                int tot;
+                int pos = written + block_excl_scan(__popc(word), scratch, &tot);
+                if (w0 + t < w1) {
+                    unsigned wbits = word;
+                    while (wbits) {
+                        const int kk = (w0 + t) * 32 + __ffs(wbits) - 1;
+                        wbits &= wbits - 1;
+                        const float v = st[kk];
+                        st[kk] = 0.f;
+                        if (pos < nnz_row) {
+                            colC[out + pos] = pc0 + kk;
+                            valC[out + pos] = v;
+                        }
+                        ++pos;
+                    }
+                    bm[w0 + t] = 0u;
+                }
+                written += tot;
+                __syncthreads();
+            }
+            cur = nxt;
+            nxt = nxt2;
+        }
+        if (t == 0 && written != nnz_row) set_status(ctl, ST_INTERNAL);
+    }
+}
+
 // ---------------------------------------------------------------------------
 
 static size_t num_warp_smem(size_t acc) { return (acc + 4) * kWarpsPerBlockNW * kWarpTableNum; }
@@ -538,6 +728,11 @@ static size_t num_block_smem(const spgemm_plan* p, size_t acc) {
 }
 // kMode 0: fp32 values and a bitmap over three table panels; kMode 1: fp64
 // values, fp32 group sums and two bitmaps over one panel
+static size_t num_dense_hot_smem(const spgemm_plan* p) {
+    return sizeof(double) * kHotWarps * kHotSlots + 4 * (size_t)p->opts.panel_cols +
+           (size_t)p->opts.panel_cols / 8;
+}
+
 static size_t num_dense_smem(const spgemm_plan* p, int mode) {
     const size_t W = (size_t)p->opts.panel_cols * (mode == 0 ? 3 : 1);
     return mode == 0 ? 4 * W + W / 8 : 12 * W + W / 4;
@@ -556,6 +751,7 @@ void occupancy_numeric(spgemm_plan* p) {
         {(const void*)k_num_block<double>, kNumBlockThreads, num_block_smem(p, 8), &p->occ_num_block64},
         {(const void*)k_num_dense<0>, kNumDenseThreads, num_dense_smem(p, 0), &p->occ_num_dense32},
         {(const void*)k_num_dense<1>, kNumDenseThreads, num_dense_smem(p, 1), &p->occ_num_dense64},
+        {(const void*)k_num_dense_hot, kHotThreads, num_dense_hot_smem(p), &p->occ_num_dense_hot},
     };
     for (auto& k : ks) {
         cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
@@ -629,6 +825,14 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                k_num_dense<0><<<sms * p->occ_num_dense32, kNumDenseThreads, num_dense_smem(p, 0), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
                    NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW));
+    if (w.bhot && w.bpanel) {
+        SPG_LAUNCH(p, K_NUM_DENSE64, s,
+                   k_num_dense_hot<<<sms * p->occ_num_dense_hot, kHotThreads, num_dense_hot_smem(p), s>>>(
+                       A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
+                       NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW, w.hot_rank, w.hot_col,
+                       w.bhot));
+        return;
+    }
     SPG_LAUNCH(p, K_NUM_DENSE64, s,
                k_num_dense<1><<<sms * p->occ_num_dense64, kNumDenseThreads, num_dense_smem(p, 1), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,

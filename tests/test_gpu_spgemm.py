@@ -90,6 +90,32 @@ def test_dense_tier_long_a_rows(plan):
     check_product(plan, A, B)
 
 
+def test_dense_tier_hot_columns(plan):
+    # B rows all hold a few hub columns, and 700 columns of the first panel sit
+    # in 300 rows each: hot columns (more than 167 entries) under contention,
+    # and a panel with more hot columns than one pass has fp64 slots
+    rng = np.random.default_rng(21)
+    rows, cols = 2000, 40000
+    hubs = np.array([5, 17, 9000, 30001])
+    warm = rng.choice(16384, size=700, replace=False)
+    r, c = [], []
+    for i in range(rows):
+        cc = set(rng.choice(cols, size=rng.integers(5, 40), replace=False).tolist())
+        cc |= set(hubs.tolist())
+        cc |= set(warm[rng.random(warm.size) < 300 / rows].tolist())
+        cc = np.array(sorted(cc))
+        r.append(np.full(cc.size, i))
+        c.append(cc)
+    r, c = np.concatenate(r), np.concatenate(c)
+    B = gen.csr_from_coo(rows, cols, r, c, gen.uniform_open_closed(rng, r.size))
+    counts = np.bincount(B.col, minlength=cols)
+    assert (counts[:16384] > 167).sum() > 512
+    A = hub_matrix(30, rows, 22, heavy_rows={0, 3, 9, 29}, heavy_len=1500, light_deg=400)
+    assert np.diff(A.row_ptr).max() > 1024 and np.sort(np.diff(A.row_ptr))[-5] > 167
+    assert oracle.symbolic(A, B).max() > 8192
+    check_product(plan, A, B)
+
+
 def test_dense_tier_unsorted_b(plan):
     B = hub_matrix(500, 50000, 7, heavy_rows=set(range(0, 500, 3)), heavy_len=400)
     Bu = gen.random_csr(1, 1, 1.0, 0)  # placeholder for type
