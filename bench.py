@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--gnn-graphs", type=int, default=8192)
     ap.add_argument("--panel-cols", type=int, default=None)
     ap.add_argument("--served-requests", type=int, default=32)
+    ap.add_argument("--row-stride", type=int, default=1,
+                    help="left operand of A*A = every k-th row of A (a smaller case with the "
+                         "same row mix and the full right operand, for profiling; not the "
+                         "headline workload, no end-to-end leg)")
     return ap.parse_args()
 
 
@@ -62,7 +66,9 @@ def workload(scale: int):
     return A, S, St, clusters
 
 
-def workload_name(scale: int) -> str:
+def workload_name(scale: int, row_stride: int = 1) -> str:
+    if row_stride > 1:
+        return f"rmat{scale}_ef16_AxA_rows1in{row_stride}_plus_StAS"
     return f"rmat{scale}_ef16_AxA_plus_StAS"
 
 
@@ -408,15 +414,22 @@ def run_ours(args):
     A = DeviceCSR.from_host(A_h, dev)
     S = DeviceCSR.from_host(S_h, dev)
     St = DeviceCSR.from_host(St_h, dev)
+    if args.row_stride > 1:
+        from paper_2512_12036_gb300 import gen
+        L_h = gen.sample_rows(A_h, args.row_stride)
+        L = DeviceCSR.from_host(L_h, dev)
+        args.no_e2e = True
+    else:
+        L_h, L = A_h, A
     opts = {}
     if args.panel_cols:
         opts["panel_cols"] = args.panel_cols
     plan = Plan(device=local, **opts)
-    ws_aa = plan.workspace(A, A)
+    ws_aa = plan.workspace(L, A)
     ws_sa = plan.workspace(St, A)
 
     # first pass: sizes and output buffers (untimed)
-    blocks, ip_aa, nnz_aa = plan.spgemm_blocks(A, A, ws=ws_aa)
+    blocks, ip_aa, nnz_aa = plan.spgemm_blocks(L, A, ws=ws_aa)
     T_blocks, ip_sa, _ = plan.spgemm_blocks(St, A, ws=ws_sa)
     T = T_blocks[0][2]
     ws_ts = plan.workspace(T, S)
@@ -428,7 +441,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        plan.spgemm_blocks(A, A, ws=ws_aa, out=blocks)
+        plan.spgemm_blocks(L, A, ws=ws_aa, out=blocks)
         plan.spgemm_blocks(St, A, ws=ws_sa, out=T_blocks)
         plan.spgemm_blocks(T, S, ws=ws_ts, out=C2_blocks)
 
@@ -468,10 +481,10 @@ def run_ours(args):
     value = 2.0 * ip_step * world / (ms_step / 1e3) / 1e9
 
     # ---- per-kernel roofline for the dominant kernel
-    ip_row = torch.empty(A.rows, dtype=torch.int64, device=dev)
-    ip_row, _ = plan.count(A, A, ws_aa, ip_row=ip_row)
-    nnz_row, _ = plan.symbolic(A, A, ip_row, ws_aa)
-    work = tier_work(plan, A_h, ip_row.cpu().numpy(), nnz_row.to(torch.int64).cpu().numpy())
+    ip_row = torch.empty(L.rows, dtype=torch.int64, device=dev)
+    ip_row, _ = plan.count(L, A, ws_aa, ip_row=ip_row)
+    nnz_row, _ = plan.symbolic(L, A, ip_row, ws_aa)
+    work = tier_work(plan, L_h, ip_row.cpu().numpy(), nnz_row.to(torch.int64).cpu().numpy())
     top = max(prof.items(), key=lambda kv: kv[1][0])
     top_name, (top_ms, top_n) = top
     peaks = {}
@@ -492,7 +505,7 @@ def run_ours(args):
                 "launches_per_step": top_n / args.steps,
                 "bytes_per_step": int(bytes_step),
                 "share_of_step": top_ms / ms}
-    compulsory = (4 * (A.rows + 1) + 8 * A.nnz) + (8 * ip_aa + 8 * A.nnz) + (8 * nnz_aa + 4 * (A.rows + 1))
+    compulsory = (4 * (L.rows + 1) + 8 * L.nnz) + (8 * ip_aa + 8 * L.nnz) + (8 * nnz_aa + 4 * (L.rows + 1))
     step_frac = compulsory / (ms_step / 1e3) / (peak_gbs * 1e9)
 
     # ---- end to end through the public API from pinned host buffers
@@ -566,7 +579,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (fp64 accumulation where "
             "more than 167 terms can meet)", "data": "synthetic",
-            "config": {"workload": workload_name(args.scale), "rmat_scale": args.scale,
+            "config": {"workload": workload_name(args.scale, args.row_stride),
+                       "rmat_scale": args.scale, "row_stride_AxA": args.row_stride,
                        "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05],
                        "nnz_A": A.nnz, "clusters": clusters, "ip_step": ip_step,
                        "ip_AxA": ip_aa, "nnz_AxA": nnz_aa, "row_blocks_AxA": n_blocks,

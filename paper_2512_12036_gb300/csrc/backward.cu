@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kBwdBlockThreads) k_bwd_panel(BwdArgs x, int b
     if (begin >= end) return;
     const int warp = threadIdx.x >> 5, lane = lane_id(), nwarps = blockDim.x >> 5;
     for (int c = threadIdx.x; c < kBwdPanel; c += blockDim.x) dense[c] = 0.f;
-    const bool use_tab = x.tab != nullptr && x.ctl->b_unsorted == 0;
+    const bool use_tab = x.tab != nullptr && (x.ctl->b_unsorted & 1) == 0;
     const int per = kBwdPanel / x.PW;                    // table panels per pass
     const int npass = (int)((x.B.cols + (long long)kBwdPanel - 1) / kBwdPanel);
     for (;;) {

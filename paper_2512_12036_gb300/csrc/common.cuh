@@ -26,7 +26,8 @@ enum : int {
 // Control block at the start of every workspace (256-byte aligned).
 struct Ctl {
     int status;
-    int b_unsorted;             // set when some row of B is not sorted by column
+    int b_unsorted;             // bit 0: a row of B is not sorted by column;
+                                // bit 1: a sorted row of B repeats a column
     int pad0[2];
     long long totals[8];        // 0: IP total, 1: nnz total, 2: scan total
     int work[kMaxTiers];        // dynamic row counters of the block-per-row tiers
@@ -285,8 +286,10 @@ struct ExpandTile {
 // so 32 products never span more than 32 of them). Loads coalesce along
 // each segment. Products are handled kUnroll steps at a time: load(t) for
 // all of them first (independent loads in flight), then apply(item, a) in
-// order. Ends with a block barrier.
-template <int kT, typename Acc, int kUnroll, class Load, class Apply>
+// order. With kSeg, apply(item, a, seg) also gets the product's segment
+// index (its entry's rank among the tile's non-empty entries). Ends with a
+// block barrier.
+template <int kT, typename Acc, int kUnroll, bool kSeg = false, class Load, class Apply>
 __device__ __forceinline__ void expand_tile(ExpandTile<kT, Acc>& sm, int bs, int len, Acc a,
                                             Load&& load, Apply&& apply) {
     using Item = decltype(load(0));
@@ -325,15 +328,18 @@ __device__ __forceinline__ void expand_tile(ExpandTile<kT, Acc>& sm, int bs, int
             int tq[kUnroll];
             Acc aq[kUnroll];
             bool vq[kUnroll];
+            int sq[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
                 vq[u] = false;
                 tq[u] = 0;
                 aq[u] = Acc(0);
+                sq[u] = 0;
                 if (base < wend) {                       // warp-uniform
                     if (base + 32 <= se) {               // the 32 products lie in segment s
                         tq[u] = sbs + (int)(base - so) + lane;
                         aq[u] = sa;
+                        sq[u] = s;
                         vq[u] = base + lane < wend;
                         base += 32;
                         if (base == se && s + 1 < nE) {
@@ -353,6 +359,7 @@ __device__ __forceinline__ void expand_tile(ExpandTile<kT, Acc>& sm, int bs, int
                         const int src = warp_find_src(rel, lane);
                         tq[u] = __shfl_sync(kFull, wbs, src) + (lane - __shfl_sync(kFull, rel, src));
                         aq[u] = __shfl_sync(kFull, wa, src);
+                        sq[u] = s + src;
                         vq[u] = base + lane < wend;
                         // segment of base + 32
                         const int cnt = __popc(__ballot_sync(kFull, rel <= 32));
@@ -372,8 +379,12 @@ __device__ __forceinline__ void expand_tile(ExpandTile<kT, Acc>& sm, int bs, int
             for (int u = 0; u < kUnroll; ++u)
                 if (vq[u]) it[u] = load(tq[u]);
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                if (vq[u]) apply(it[u], aq[u]);
+            for (int u = 0; u < kUnroll; ++u) {
+                if (vq[u]) {
+                    if constexpr (kSeg) apply(it[u], aq[u], sq[u]);
+                    else apply(it[u], aq[u]);
+                }
+            }
         }
     }
     __syncthreads();

@@ -290,8 +290,9 @@ __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev
 // ---------------------------------------------------------------------------
 // Panel offset table of B: for row k and panel p, tab[k*(P+1)+p] is the
 // first position of row k whose column is >= p*PW (valid when rows are
-// sorted; an unsorted row sets ctl->b_unsorted and the dense tier then
-// filters whole B rows instead).
+// sorted; an unsorted row sets bit 0 of ctl->b_unsorted and the dense tier
+// then filters whole B rows instead; a sorted row that repeats a column sets
+// bit 1).
 __global__ void k_bpanel(CsrDev B, int P, int PW, int* tab, Ctl* ctl) {
     const int lane = lane_id();
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -302,7 +303,7 @@ __global__ void k_bpanel(CsrDev B, int P, int PW, int* tab, Ctl* ctl) {
             for (int p = lane; p <= P; p += 32) tab[k * (P + 1) + p] = 0;
             continue;
         }
-        bool unsorted = false;
+        bool unsorted = false, dup = false;
         for (int t = s + lane; t <= e; t += 32) {
             int prev = -1, cur = P;
             if (t > s) {
@@ -313,10 +314,12 @@ __global__ void k_bpanel(CsrDev B, int P, int PW, int* tab, Ctl* ctl) {
                 const int c = B.col[t];
                 cur = c < 0 ? 0 : (c / PW >= P ? P - 1 : c / PW);
                 if (t > s && c < B.col[t - 1]) unsorted = true;
+                if (t > s && c == B.col[t - 1]) dup = true;
             }
             for (int p = prev + 1; p <= cur; ++p) tab[k * (P + 1) + p] = t;
         }
-        if (__any_sync(kFull, unsorted) && lane == 0) atomicExch(&ctl->b_unsorted, 1);
+        const int flags = (__any_sync(kFull, unsorted) ? 1 : 0) | (__any_sync(kFull, dup) ? 2 : 0);
+        if (flags && lane == 0) atomicOr(&ctl->b_unsorted, flags);
     }
 }
 
@@ -341,6 +344,9 @@ __global__ void k_bpanel(CsrDev B, int P, int PW, int* tab, Ctl* ctl) {
 // their entries (and the panel table) in tiles every pass.
 constexpr int kGroup = 160;
 
+#ifndef SPG_D32_UNROLL
+#define SPG_D32_UNROLL 4
+#endif
 template <int kMode>
 __global__ void __launch_bounds__(kNumDenseThreads, 1) k_num_dense(CsrDev A, CsrDev B,
                                                                    const int* map, Ctl* ctl,
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(kNumDenseThreads, 1) k_num_dense(CsrDev A, Csr
         bm[i] = 0u;
         if (kMode == 1) gbm[i] = 0u;
     }
-    const bool use_tab = tab != nullptr && ctl->b_unsorted == 0;
+    const bool use_tab = tab != nullptr && (ctl->b_unsorted & 1) == 0;
     const int npass = (int)((B.cols + (long long)W - 1) / W);
     const long long stride = P + 1;
     unsigned* obm = kMode == 1 ? gbm : bm;             // bitmap the products mark
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(kNumDenseThreads, 1) k_num_dense(CsrDev A, Csr
                     }
                 }
                 if (kMode == 0) {
-                    expand_tile<kNumDenseThreads, float, 4>(tile, bs, len, mya, load, apply);
+                    expand_tile<kNumDenseThreads, float, SPG_D32_UNROLL>(tile, bs, len, mya, load, apply);
                 } else {
                     for (int g0 = 0; g0 < na; g0 += kGroup) {
                         const bool mine = (int)threadIdx.x >= g0 && (int)threadIdx.x < g0 + kGroup;
@@ -532,17 +538,33 @@ __global__ void __launch_bounds__(kNumDenseThreads, 1) k_num_dense(CsrDev A, Csr
 
 // Heavy rows whose entries can gather more than fp32_max_terms products
 // (the fp64 tier). Products on cold columns of B (see hot.cu) are summed in
-// fp32 exactly as in the fp32 tier; products on hot columns go to per-warp
-// private fp64 partial sums in shared memory (one slot per hot column of the
-// pass), which keeps the fp64 atomics free of cross-warp contention on the
-// hub columns that R-MAT rows all share. After a pass the warps' partials
-// are added (fp64), rounded once into the pass array and emitted with the
-// cold columns in column order. A pass covers one table panel; when a panel
-// holds more hot columns than there are slots it is split into sub-passes
-// at hot-column boundaries (re-reading the panel's segments).
-constexpr int kHotSlots = 512;
+// fp32 exactly as in the fp32 tier. Products on hot columns (one slot per
+// hot column of the sub-pass) are split over kCopies fp32 partial sums by
+// the rank of their A entry in the expansion tile (rank mod kCopies): with
+// at most kHotThreads entries in a tile and each entry adding at most one
+// product to a column (B rows sorted, no repeated column), a copy gathers
+// at most kHotThreads / kCopies = 128 terms per column. After every tile
+// the copies are added into an fp64 accumulator in a fixed order and
+// cleared; at the end of the sub-pass the accumulator is rounded once into
+// the pass array. The error stays within (gamma_128 + u) * sum|a||b| plus
+// fp64 rounding, below the 1e-5 bound, with fp32 shared-memory atomics only.
+// When B has unsorted or repeated columns (ctl->b_unsorted != 0) the bound
+// does not hold and hot-column products go straight to the fp64
+// accumulator with fp64 atomics instead.
+//
+// A pass covers ppp table panels (as many as shared memory holds, set at
+// launch); when it holds more hot columns than kSlots it is split into
+// sub-passes at hot-column boundaries (re-reading its segments).
 constexpr int kHotThreads = 1024;
-constexpr int kHotWarps = kHotThreads / 32;
+#ifndef SPG_HOT_UNROLL
+#define SPG_HOT_UNROLL 2
+#endif
+#ifndef SPG_HOT_SLOTS
+#define SPG_HOT_SLOTS 1024
+#endif
+constexpr int kHotSlots = SPG_HOT_SLOTS;
+constexpr int kHotCopies = 8;
+static_assert(kHotThreads / kHotCopies <= 160, "a copy must gather at most 160 terms per tile");
 
 struct KeyValHot {
     int key;
@@ -556,48 +578,67 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                                                                   int* colC, float* valC,
                                                                   int bin_lo, int bin_hi, int tier,
                                                                   const int* tab, int P, int PW,
-                                                                  const int* hot_rank,
+                                                                  int ppp, const int* hot_rank,
                                                                   const int* hot_col,
                                                                   const int* bhot) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    double* priv = reinterpret_cast<double*>(sm_raw);                 // [kHotWarps][kHotSlots]
-    float* st = reinterpret_cast<float*>(sm_raw + sizeof(double) * kHotWarps * kHotSlots);
-    unsigned* bm = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(st) +
-                                               sizeof(float) * PW);
+    const int W = PW * ppp;                                           // columns per pass
+    double* acc = reinterpret_cast<double*>(sm_raw);                  // [kHotSlots]
+    float* cp = reinterpret_cast<float*>(acc + kHotSlots);            // [kHotCopies][kHotSlots]
+    float* st = cp + kHotCopies * kHotSlots;                          // [W]
+    unsigned* bm = reinterpret_cast<unsigned*>(st + W);               // [W / 32]
     __shared__ int s_idx;
     __shared__ int scratch[33];
     __shared__ ExpandTile<kHotThreads, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
     if (begin >= end) return;
-    const int t = threadIdx.x, warp = t >> 5;
-    const int nwords = PW >> 5;
-    for (int i = t; i < PW; i += kHotThreads) st[i] = 0.f;
+    const int t = threadIdx.x;
+    const int nwords = W >> 5;
+    for (int i = t; i < W; i += kHotThreads) st[i] = 0.f;
     for (int i = t; i < nwords; i += kHotThreads) bm[i] = 0u;
-    for (int i = t; i < kHotWarps * kHotSlots; i += kHotThreads) priv[i] = 0.0;
-    const bool use_tab = tab != nullptr && ctl->b_unsorted == 0;
-    const int npass = P;                                  // one table panel per pass
+    for (int i = t; i < kHotSlots; i += kHotThreads) acc[i] = 0.0;
+    for (int i = t; i < kHotCopies * kHotSlots; i += kHotThreads) cp[i] = 0.f;
+    const bool use_tab = tab != nullptr && (ctl->b_unsorted & 1) == 0;
+    const bool split = ctl->b_unsorted == 0;       // copies bound the terms per column
+    const int npass = (P + ppp - 1) / ppp;
     const long long stride = P + 1;
-    double* mypriv = priv + warp * kHotSlots;
 
-    int pc0 = 0, lo = 0, hi = 0, hr0 = 0;                 // panel start, sub-pass [lo, hi)
+    int pc0 = 0, lo = 0, hi = 0, hr0 = 0;                 // pass start, sub-pass [lo, hi)
     auto load = [&](int q) { return KeyValHot{B.col[q], B.val[q], bhot[q]}; };
-    auto apply = [&](KeyValHot kv, float a) {
+    auto apply = [&](KeyValHot kv, float a, int seg) {
         if (!key_in(kv.key, B, ctl)) return;
         if (kv.key < lo || kv.key >= hi) {
-            if (use_tab && (kv.key < pc0 || kv.key >= pc0 + PW)) set_status(ctl, ST_INTERNAL);
+            if (use_tab && (kv.key < pc0 || kv.key >= pc0 + W)) set_status(ctl, ST_INTERNAL);
             return;
         }
         const int kk = kv.key - pc0;
         atomicOr(&bm[kk >> 5], 1u << (kk & 31));
         if (kv.hot >= 0) {
             const int slot = kv.hot - hr0;
-            if ((unsigned)slot < (unsigned)kHotSlots)
-                atomicAdd(&mypriv[slot], (double)a * (double)kv.v);
-            else
+            if ((unsigned)slot >= (unsigned)kHotSlots) {
                 set_status(ctl, ST_INTERNAL);
+            } else if (split) {
+                atomicAdd(&cp[(seg & (kHotCopies - 1)) * kHotSlots + slot], a * kv.v);
+            } else {
+                atomicAdd(&acc[slot], (double)a * (double)kv.v);
+            }
         } else {
             atomicAdd(&st[kk], a * kv.v);
         }
+    };
+    // add the copies of this sub-pass's hot slots into the fp64 accumulator
+    auto fold = [&]() {
+        const int nh = hot_rank[hi] - hr0;
+        for (int h = t; h < nh; h += kHotThreads) {
+            double v = acc[h];
+#pragma unroll
+            for (int c = 0; c < kHotCopies; ++c) {
+                v += (double)cp[c * kHotSlots + h];
+                cp[c * kHotSlots + h] = 0.f;
+            }
+            acc[h] = v;
+        }
+        __syncthreads();
     };
 
     for (;;) {
@@ -623,18 +664,20 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                 myk = k;
                 mya = A.val[j];
                 cur = tab[(long long)k * stride];
-                nxt = tab[(long long)k * stride + (P > 0 ? 1 : 0)];
+                nxt = tab[(long long)k * stride + (ppp < P ? ppp : P)];
             } else {
                 set_status(ctl, ST_INVALID);
             }
         }
         int written = 0;
         for (int pass = 0; pass < npass; ++pass) {
-            pc0 = pass * PW;
-            const int pc1 = (int)(B.cols - (long long)pc0 < PW ? B.cols : pc0 + PW);
+            pc0 = pass * W;
+            const int pc1 = (int)(B.cols - (long long)pc0 < W ? B.cols : pc0 + W);
+            const int p0 = pass * ppp;
+            const int p1 = p0 + ppp < P ? p0 + ppp : P;
             int nxt2 = 0;
             if (cached && myk >= 0 && pass + 1 < npass)
-                nxt2 = tab[(long long)myk * stride + pass + 2];
+                nxt2 = tab[(long long)myk * stride + (p1 + ppp < P ? p1 + ppp : P)];
             int bs = 0, len = 0;
             if (cached && myk >= 0) {
                 if (cur < 0 || nxt < cur || (long long)nxt > B.nnz) set_status(ctl, ST_INTERNAL);
@@ -653,7 +696,9 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                     hi = pc1;
                 }
                 if (cached) {
-                    expand_tile<kHotThreads, float, 4>(tile, bs, len, mya, load, apply);
+                    expand_tile<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, bs, len, mya, load,
+                                                                          apply);
+                    fold();
                 } else {
                     for (int tb = rs; tb < re; tb += kHotThreads) {
                         const int j = tb + t;
@@ -664,7 +709,7 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                             a = A.val[j];
                             if (use_tab && tlen > 0) {
                                 const int* tk = tab + (long long)A.col[j] * stride;
-                                const int ps = tk[pass], pe = tk[pass + 1];
+                                const int ps = tk[p0], pe = tk[p1];
                                 if (ps >= tbs && pe >= ps && pe <= tbs + tlen) {
                                     tbs = ps;
                                     tlen = pe - ps;
@@ -674,31 +719,35 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                                 }
                             }
                         }
-                        expand_tile<kHotThreads, float, 4>(tile, tbs, tlen, a, load, apply);
+                        expand_tile<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, tbs, tlen, a,
+                                                                              load, apply);
+                        fold();
                     }
                 }
-                // fold the warps' fp64 partials of the hot columns into the pass array
-                const int nh = (hot_rank[hi] - hr0);
+                // round the hot columns' sums once into the pass array
+                const int nh = hot_rank[hi] - hr0;
                 for (int h = t; h < nh; h += kHotThreads) {
-                    double v = 0.0;
-                    for (int w2 = 0; w2 < kHotWarps; ++w2) {
-                        v += priv[w2 * kHotSlots + h];
-                        priv[w2 * kHotSlots + h] = 0.0;
-                    }
                     const int kk = hot_col[hr0 + h] - pc0;
-                    if ((unsigned)kk < (unsigned)PW) st[kk] = (float)v;
+                    if ((unsigned)kk < (unsigned)W) st[kk] = (float)acc[h];
+                    acc[h] = 0.0;
                 }
                 __syncthreads();
                 // emit [lo, hi) in column order (bits outside it are clear)
                 const int w0 = (lo - pc0) >> 5;
                 const int w1 = (hi - pc0 + 31) >> 5;
-                const unsigned word = (w0 + t < w1) ? bm[w0 + t] : 0u;
+                const int wpt = (w1 - w0 + kHotThreads - 1) / kHotThreads;
+                const int wb = w0 + t * wpt;
+                int cnt = 0;
+                for (int q = 0; q < wpt; ++q)
+                    if (wb + q < w1) cnt += __popc(bm[wb + q]);
                 int tot;
-                int pos = written + block_excl_scan(__popc(word), scratch, &tot);
-                if (w0 + t < w1) {
-                    unsigned wbits = word;
+                int pos = written + block_excl_scan(cnt, scratch, &tot);
+                for (int q = 0; q < wpt; ++q) {
+                    const int wq = wb + q;
+                    if (wq >= w1) break;
+                    unsigned wbits = bm[wq];
                     while (wbits) {
-                        const int kk = (w0 + t) * 32 + __ffs(wbits) - 1;
+                        const int kk = wq * 32 + __ffs(wbits) - 1;
                         wbits &= wbits - 1;
                         const float v = st[kk];
                         st[kk] = 0.f;
@@ -708,7 +757,7 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                         }
                         ++pos;
                     }
-                    bm[w0 + t] = 0u;
+                    bm[wq] = 0u;
                 }
                 written += tot;
                 __syncthreads();
@@ -720,18 +769,24 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
     }
 }
 
+// shared memory of the fp64 tier for ppp panels of pw columns per pass
+constexpr size_t hot_smem_of(int pw, int ppp) {
+    return (sizeof(double) + sizeof(float) * kHotCopies) * kHotSlots + 4 * (size_t)pw * ppp +
+           (size_t)pw * ppp / 8;
+}
+
 // ---------------------------------------------------------------------------
 
 static size_t num_warp_smem(size_t acc) { return (acc + 4) * kWarpsPerBlockNW * kWarpTableNum; }
 static size_t num_block_smem(const spgemm_plan* p, size_t acc) {
     return (acc + 4) * pow2_ceil(2u * (unsigned)p->opts.block_max_nnz);
 }
+static size_t num_dense_hot_smem(const spgemm_plan* p) {
+    return hot_smem_of(p->opts.panel_cols, p->hot_ppp);
+}
+
 // kMode 0: fp32 values and a bitmap over three table panels; kMode 1: fp64
 // values, fp32 group sums and two bitmaps over one panel
-static size_t num_dense_hot_smem(const spgemm_plan* p) {
-    return sizeof(double) * kHotWarps * kHotSlots + 4 * (size_t)p->opts.panel_cols +
-           (size_t)p->opts.panel_cols / 8;
-}
 
 static size_t num_dense_smem(const spgemm_plan* p, int mode) {
     const size_t W = (size_t)p->opts.panel_cols * (mode == 0 ? 3 : 1);
@@ -739,6 +794,16 @@ static size_t num_dense_smem(const spgemm_plan* p, int mode) {
 }
 
 void occupancy_numeric(spgemm_plan* p) {
+    // fp64 dense tier: as many table panels per pass as the shared memory
+    // left beside its static arrays holds
+    {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, (const void*)k_num_dense_hot);
+        const size_t fixed = hot_smem_of(p->opts.panel_cols, 0) + fa.sharedSizeBytes;
+        const size_t per = hot_smem_of(p->opts.panel_cols, 1) - hot_smem_of(p->opts.panel_cols, 0);
+        p->hot_ppp = p->smem_optin > fixed + per ? (int)((p->smem_optin - fixed) / per) : 1;
+        if (p->hot_ppp > 64) p->hot_ppp = 64;
+    }
     struct K {
         const void* f;
         int threads;
@@ -829,8 +894,8 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
         SPG_LAUNCH(p, K_NUM_DENSE64, s,
                    k_num_dense_hot<<<sms * p->occ_num_dense_hot, kHotThreads, num_dense_hot_smem(p), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
-                       NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW, w.hot_rank, w.hot_col,
-                       w.bhot));
+                       NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW, p->hot_ppp,
+                       w.hot_rank, w.hot_col, w.bhot));
         return;
     }
     SPG_LAUNCH(p, K_NUM_DENSE64, s,

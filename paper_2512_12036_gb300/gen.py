@@ -212,6 +212,21 @@ def random_csr(rows: int, cols: int, density: float, seed: int, *, duplicates: b
     return csr
 
 
+def sample_rows(A: HostCSR, stride: int) -> HostCSR:
+    """Rows 0, stride, 2*stride, ... of A (same columns): a smaller left
+    operand with the row-length mix of the whole matrix."""
+    if stride < 1:
+        raise ValueError("stride must be >= 1")
+    rp = A.row_ptr.astype(np.int64)
+    pick = np.arange(0, A.rows, stride)
+    lens = rp[pick + 1] - rp[pick]
+    row_ptr = np.zeros(pick.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    idx = np.repeat(rp[pick] - row_ptr[:-1], lens) + np.arange(int(row_ptr[-1]))
+    return HostCSR(int(pick.size), A.cols, row_ptr.astype(np.int32), A.col[idx].copy(),
+                   A.val[idx].copy())
+
+
 def transpose_structure(A: HostCSR) -> HostCSR:
     """Plain re-layout of A as A^T (no arithmetic on values)."""
     r = np.repeat(np.arange(A.rows, dtype=np.int64), np.diff(A.row_ptr.astype(np.int64)))

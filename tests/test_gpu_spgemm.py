@@ -91,13 +91,13 @@ def test_dense_tier_long_a_rows(plan):
 
 
 def test_dense_tier_hot_columns(plan):
-    # B rows all hold a few hub columns, and 700 columns of the first panel sit
+    # B rows all hold a few hub columns, and 1400 columns of the first panel sit
     # in 300 rows each: hot columns (more than 167 entries) under contention,
-    # and a panel with more hot columns than one pass has fp64 slots
+    # and a pass with more hot columns than it has fp64 slots (1024)
     rng = np.random.default_rng(21)
     rows, cols = 2000, 40000
     hubs = np.array([5, 17, 9000, 30001])
-    warm = rng.choice(16384, size=700, replace=False)
+    warm = rng.choice(16384, size=1400, replace=False)
     r, c = [], []
     for i in range(rows):
         cc = set(rng.choice(cols, size=rng.integers(5, 40), replace=False).tolist())
@@ -109,11 +109,59 @@ def test_dense_tier_hot_columns(plan):
     r, c = np.concatenate(r), np.concatenate(c)
     B = gen.csr_from_coo(rows, cols, r, c, gen.uniform_open_closed(rng, r.size))
     counts = np.bincount(B.col, minlength=cols)
-    assert (counts[:16384] > 167).sum() > 512
+    assert (counts[:16384] > 167).sum() > 1100
     A = hub_matrix(30, rows, 22, heavy_rows={0, 3, 9, 29}, heavy_len=1500, light_deg=400)
     assert np.diff(A.row_ptr).max() > 1024 and np.sort(np.diff(A.row_ptr))[-5] > 167
     assert oracle.symbolic(A, B).max() > 8192
     check_product(plan, A, B)
+
+
+def test_dense_tier_repeated_columns_in_b(plan):
+    # sorted B rows that repeat a column (hub columns twice): the fp64 tier's
+    # per-copy term bound needs distinct columns, so these products take the
+    # fp64 accumulator path
+    rng = np.random.default_rng(31)
+    rows, cols = 500, 50000
+    r, c = [], []
+    for i in range(rows):
+        cc = list(rng.choice(cols, size=40, replace=False)) + [5, 77]
+        if i % 2 == 0:
+            cc += [5, 77, 77]
+        r.append(np.full(len(cc), i))
+        c.append(np.array(cc))
+    r, c = np.concatenate(r), np.concatenate(c)
+    B = gen.csr_from_coo(rows, cols, r, c, gen.uniform_open_closed(rng, r.size))
+    assert (np.diff(B.col[B.row_ptr[0]:B.row_ptr[1]]) == 0).any()
+    A = hub_matrix(50, rows, 32, heavy_rows={0, 10, 20}, heavy_len=300)
+    assert oracle.symbolic(A, B).max() > 8192
+    check_product(plan, A, B)
+
+
+def test_dense_tier_small_terms_after_large(plan):
+    # one row of 1024 ones against B rows that all hold column 0 (a hot
+    # column): B[0,0] = 1 and B[k,0] = 2^-25 for k > 0. A single fp32 running
+    # sum that takes the 1 first loses every small term (3e-5 of the sum);
+    # the tier's partial sums must stay within the 1e-5 bound
+    rng = np.random.default_rng(41)
+    na, cols = 1024, 40000
+    r, c, v = [], [], []
+    for k in range(na):
+        cc = np.concatenate([[0], 1 + rng.choice(cols - 1, size=16, replace=False)])
+        vv = gen.uniform_open_closed(rng, cc.size)
+        vv[0] = 1.0 if k == 0 else 2.0 ** -25
+        r.append(np.full(cc.size, k))
+        c.append(cc)
+        v.append(vv)
+    B = gen.csr_from_coo(na, cols, np.concatenate(r), np.concatenate(c),
+                         np.concatenate(v).astype(np.float32))
+    A = gen.csr_from_coo(2, na, np.zeros(na, np.int64), np.arange(na),
+                         np.ones(na, np.float32))
+    assert oracle.symbolic(A, B).max() > 8192
+    got = run(plan, A, B)
+    ref = oracle.spgemm(A, B)
+    compare(got, ref)
+    assert got.col[0] == 0
+    assert abs(float(got.val[0]) - (1.0 + 1023 * 2.0 ** -25)) <= 1e-5 * ref.bound[0]
 
 
 def test_dense_tier_unsorted_b(plan):
