@@ -39,6 +39,7 @@ struct spgemm_plan {
     int occ_num_warp32, occ_num_warp64, occ_num_block32, occ_num_block64;
     int occ_num_dense32, occ_num_dense64, occ_num_dense_hot;
     int hot_ppp;           // table panels per pass of the fp64 dense tier
+    int d32_ppp;           // and of the fp32 dense tier
 };
 
 namespace spg {

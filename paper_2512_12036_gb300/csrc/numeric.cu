@@ -137,6 +137,98 @@ __device__ __forceinline__ void bitonic_sort(int* keys, Acc* vals, int n2, int t
     }
 }
 
+// Block-wide sort of n distinct keys keys[0, n) with their values, into
+// keys[off, off + n) (the two ranges must not overlap): keys are bucketed on
+// the high bits of key - min (about four per bucket), counted, scattered to
+// their bucket's range and each bucket is then insertion-sorted by one
+// thread. A few barriers instead of the log^2 stages of a sorting network.
+// Returns false, with keys[0, n) untouched, when some bucket would hold more
+// than kSortBucketMax keys (strongly clustered columns); the caller then
+// sorts in place by other means. cnt holds kSortBuckets ints, mm 3 ints.
+constexpr int kSortBuckets = 2048;
+constexpr int kSortBucketMax = 32;
+
+template <typename Acc>
+__device__ bool block_bucket_sort(int* keys, Acc* vals, int n, int off, int* cnt, int* mm,
+                                  int* scratch) {
+    const int tid = threadIdx.x, bd = blockDim.x;
+    int nb = (int)pow2_ceil((unsigned)((n + 3) >> 2));
+    nb = nb < 32 ? 32 : (nb > kSortBuckets ? kSortBuckets : nb);
+    const int lognb = 31 - __clz(nb);
+    for (int b = tid; b < nb; b += bd) cnt[b] = 0;
+    if (tid == 0) {
+        mm[0] = 0x7fffffff;
+        mm[1] = 0;
+        mm[2] = 0;
+    }
+    __syncthreads();
+    int lo = 0x7fffffff, hi = 0;
+    for (int t = tid; t < n; t += bd) {
+        const int k = keys[t];
+        lo = k < lo ? k : lo;
+        hi = k > hi ? k : hi;
+    }
+    lo = __reduce_min_sync(kFull, lo);
+    hi = __reduce_max_sync(kFull, hi);
+    if (lane_id() == 0) {
+        atomicMin(&mm[0], lo);
+        atomicMax(&mm[1], hi);
+    }
+    __syncthreads();
+    const int kmin = mm[0];
+    const long long span = (long long)mm[1] - kmin + 1;
+    int sh = log2_ceil_ll(span > 1 ? span : 1) - lognb;
+    sh = sh < 0 ? 0 : sh;
+    for (int t = tid; t < n; t += bd) atomicAdd(&cnt[(keys[t] - kmin) >> sh], 1);
+    __syncthreads();
+    // exclusive offsets of the buckets; largest bucket into mm[2]
+    const int cpt = (nb + bd - 1) / bd;
+    const int b0 = tid * cpt;
+    int sum = 0, big = 0;
+    for (int q = 0; q < cpt; ++q)
+        if (b0 + q < nb) {
+            const int c = cnt[b0 + q];
+            sum += c;
+            big = c > big ? c : big;
+        }
+    if (big > kSortBucketMax) atomicMax(&mm[2], big);
+    int tot;
+    int run = block_excl_scan(sum, scratch, &tot);
+    for (int q = 0; q < cpt; ++q)
+        if (b0 + q < nb) {
+            const int c = cnt[b0 + q];
+            cnt[b0 + q] = run;
+            run += c;
+        }
+    __syncthreads();
+    if (mm[2] > kSortBucketMax) return false;
+    for (int t = tid; t < n; t += bd) {
+        const int k = keys[t];
+        const int p = atomicAdd(&cnt[(k - kmin) >> sh], 1);
+        keys[off + p] = k;
+        vals[off + p] = vals[t];
+    }
+    __syncthreads();
+    // cnt[b] is now the end of bucket b
+    for (int b = tid; b < nb; b += bd) {
+        const int s0 = off + (b > 0 ? cnt[b - 1] : 0), e0 = off + cnt[b];
+        for (int i = s0 + 1; i < e0; ++i) {
+            const int k = keys[i];
+            const Acc v = vals[i];
+            int j = i - 1;
+            while (j >= s0 && keys[j] > k) {
+                keys[j + 1] = keys[j];
+                vals[j + 1] = vals[j];
+                --j;
+            }
+            keys[j + 1] = k;
+            vals[j + 1] = v;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
 template <typename Acc>
 __global__ void __launch_bounds__(kWarpsPerBlockNW * 32) k_num_warp(CsrDev A, CsrDev B,
                                                                     const int* map, Ctl* ctl,
@@ -214,6 +306,8 @@ __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev
     int* keys = reinterpret_cast<int*>(sm_raw + sizeof(Acc) * (1u << max_bits));
     __shared__ int s_idx;
     __shared__ int scratch[33];
+    __shared__ int s_cnt[kSortBuckets];
+    __shared__ int s_mm[3];
     __shared__ ExpandTile<kNumBlockThreads, Acc> tile;
     const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
     for (;;) {
@@ -275,13 +369,17 @@ __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev
         }
         if (threadIdx.x == 0 && n != nnz_row) set_status(ctl, ST_INTERNAL);
         const int nn = n < nnz_row ? n : nnz_row;
-        const int n2 = (int)pow2_ceil((unsigned)(nn > 1 ? nn : 1));
-        for (int t = nn + threadIdx.x; t < n2; t += blockDim.x) keys[t] = 0x7fffffff;
-        __syncthreads();
-        bitonic_sort<Acc, true>(keys, vals, n2, threadIdx.x, blockDim.x);
+        int so = T >> 1;                 // sorted run: keys[so, so + nn)
+        if (nn > so || !block_bucket_sort<Acc>(keys, vals, nn, so, s_cnt, s_mm, scratch)) {
+            const int n2 = (int)pow2_ceil((unsigned)(nn > 1 ? nn : 1));
+            for (int t = nn + threadIdx.x; t < n2; t += blockDim.x) keys[t] = 0x7fffffff;
+            __syncthreads();
+            bitonic_sort<Acc, true>(keys, vals, n2, threadIdx.x, blockDim.x);
+            so = 0;
+        }
         for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-            colC[out + t] = keys[t];
-            valC[out + t] = (float)vals[t];
+            colC[out + t] = keys[so + t];
+            valC[out + t] = (float)vals[so + t];
         }
         __syncthreads();
     }
@@ -347,15 +445,24 @@ constexpr int kGroup = 160;
 #ifndef SPG_D32_UNROLL
 #define SPG_D32_UNROLL 4
 #endif
-template <int kMode>
-__global__ void __launch_bounds__(kNumDenseThreads, 1) k_num_dense(CsrDev A, CsrDev B,
-                                                                   const int* map, Ctl* ctl,
-                                                                   const int* rptC, int row_begin,
-                                                                   int* colC, float* valC,
-                                                                   int bin_lo, int bin_hi,
-                                                                   int tier, const int* tab, int P,
-                                                                   int PW) {
-    constexpr int kPanelsPerPass = kMode == 0 ? 3 : 1;
+#ifndef SPG_D32_THREADS
+#define SPG_D32_THREADS 1024
+#endif
+#ifndef SPG_D32_BLOCKS
+#define SPG_D32_BLOCKS 1
+#endif
+constexpr int kD32Threads = SPG_D32_THREADS;   // fp32 dense tier: threads per block
+constexpr int kD32Blocks = SPG_D32_BLOCKS;     // and blocks per SM it is sized for
+
+template <int kMode, int kT>
+__global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B, const int* map,
+                                                            Ctl* ctl, const int* rptC,
+                                                            int row_begin, int* colC,
+                                                            float* valC, int bin_lo, int bin_hi,
+                                                            int tier, const int* tab, int P,
+                                                            int PW, int ppp) {
+    constexpr int kNumDenseThreads = kT;
+    const int kPanelsPerPass = kMode == 0 ? ppp : 1;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int W = PW * kPanelsPerPass;                 // columns per pass
     const int nwords_pass = W >> 5;
@@ -789,7 +896,7 @@ static size_t num_dense_hot_smem(const spgemm_plan* p) {
 // values, fp32 group sums and two bitmaps over one panel
 
 static size_t num_dense_smem(const spgemm_plan* p, int mode) {
-    const size_t W = (size_t)p->opts.panel_cols * (mode == 0 ? 3 : 1);
+    const size_t W = (size_t)p->opts.panel_cols * (mode == 0 ? p->d32_ppp : 1);
     return mode == 0 ? 4 * W + W / 8 : 12 * W + W / 4;
 }
 
@@ -804,6 +911,22 @@ void occupancy_numeric(spgemm_plan* p) {
         p->hot_ppp = p->smem_optin > fixed + per ? (int)((p->smem_optin - fixed) / per) : 1;
         if (p->hot_ppp > 64) p->hot_ppp = 64;
     }
+    // fp32 dense tier: as many table panels per pass as a block's share of
+    // the SM's shared memory holds beside its static arrays
+    {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, (const void*)k_num_dense<0, kD32Threads>);
+        int per_sm = 0, reserved = 0;
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, p->device);
+        size_t avail = (size_t)per_sm / kD32Blocks;
+        avail = avail > (size_t)reserved ? avail - reserved : 0;
+        if (avail > p->smem_optin) avail = p->smem_optin;
+        avail = avail > fa.sharedSizeBytes ? avail - fa.sharedSizeBytes : 0;
+        const size_t per = 4 * (size_t)p->opts.panel_cols + p->opts.panel_cols / 8;
+        p->d32_ppp = avail >= per ? (int)(avail / per) : 1;
+        if (p->d32_ppp > 64) p->d32_ppp = 64;
+    }
     struct K {
         const void* f;
         int threads;
@@ -814,8 +937,8 @@ void occupancy_numeric(spgemm_plan* p) {
         {(const void*)k_num_warp<double>, kWarpsPerBlockNW * 32, num_warp_smem(8), &p->occ_num_warp64},
         {(const void*)k_num_block<float>, kNumBlockThreads, num_block_smem(p, 4), &p->occ_num_block32},
         {(const void*)k_num_block<double>, kNumBlockThreads, num_block_smem(p, 8), &p->occ_num_block64},
-        {(const void*)k_num_dense<0>, kNumDenseThreads, num_dense_smem(p, 0), &p->occ_num_dense32},
-        {(const void*)k_num_dense<1>, kNumDenseThreads, num_dense_smem(p, 1), &p->occ_num_dense64},
+        {(const void*)k_num_dense<0, kD32Threads>, kD32Threads, num_dense_smem(p, 0), &p->occ_num_dense32},
+        {(const void*)k_num_dense<1, 1024>, 1024, num_dense_smem(p, 1), &p->occ_num_dense64},
         {(const void*)k_num_dense_hot, kHotThreads, num_dense_hot_smem(p), &p->occ_num_dense_hot},
     };
     for (auto& k : ks) {
@@ -887,9 +1010,9 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits));
     const int PW = w.panel_cols;
     SPG_LAUNCH(p, K_NUM_DENSE32, s,
-               k_num_dense<0><<<sms * p->occ_num_dense32, kNumDenseThreads, num_dense_smem(p, 0), s>>>(
+               k_num_dense<0, kD32Threads><<<sms * p->occ_num_dense32, kD32Threads, num_dense_smem(p, 0), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
-                   NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW));
+                   NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW, p->d32_ppp));
     if (w.bhot && w.bpanel) {
         SPG_LAUNCH(p, K_NUM_DENSE64, s,
                    k_num_dense_hot<<<sms * p->occ_num_dense_hot, kHotThreads, num_dense_hot_smem(p), s>>>(
@@ -899,9 +1022,9 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
         return;
     }
     SPG_LAUNCH(p, K_NUM_DENSE64, s,
-               k_num_dense<1><<<sms * p->occ_num_dense64, kNumDenseThreads, num_dense_smem(p, 1), s>>>(
+               k_num_dense<1, 1024><<<sms * p->occ_num_dense64, 1024, num_dense_smem(p, 1), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
-                   NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW));
+                   NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW, 1));
 }
 
 }  // namespace spg

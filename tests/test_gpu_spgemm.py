@@ -164,6 +164,39 @@ def test_dense_tier_small_terms_after_large(plan):
     assert abs(float(got.val[0]) - (1.0 + 1023 * 2.0 ** -25)) <= 1e-5 * ref.bound[0]
 
 
+def test_block_tier_clustered_columns(plan):
+    # rows of C with 512..8192 entries (block hash tier, fp32 and fp64 rows)
+    # whose columns crowd into [0, 3000) plus one far column: the bucket sort
+    # sees buckets far above its limit and must fall back; other rows spread
+    # their columns and take the bucket sort
+    rng = np.random.default_rng(51)
+    rows, cols = 2000, 1_000_000
+    r, c = [], []
+    for k in range(rows):
+        if k < 1000:
+            cc = rng.choice(3000, size=20, replace=False)
+            if k == 0:
+                cc = np.append(cc, cols - 1)
+        else:
+            cc = rng.choice(cols, size=20, replace=False)
+        r.append(np.full(cc.size, k))
+        c.append(cc)
+    r, c = np.concatenate(r), np.concatenate(c)
+    B = gen.csr_from_coo(rows, cols, r, c, gen.uniform_open_closed(rng, r.size))
+    ra, ca = [], []
+    for i, (lo, n) in enumerate([(0, 150), (0, 300), (1000, 150), (1000, 300), (0, 60)]):
+        cc = lo + rng.choice(1000, size=n, replace=False)
+        if i in (0, 1):
+            cc = np.append(cc[cc != 0], 0)
+        ra.append(np.full(cc.size, i))
+        ca.append(cc)
+    ra, ca = np.concatenate(ra), np.concatenate(ca)
+    A = gen.csr_from_coo(5, rows, ra, ca, gen.uniform_open_closed(rng, ra.size))
+    nnz = oracle.symbolic(A, B)
+    assert ((nnz > 512) & (nnz <= 8192)).sum() >= 4
+    check_product(plan, A, B)
+
+
 def test_dense_tier_unsorted_b(plan):
     B = hub_matrix(500, 50000, 7, heavy_rows=set(range(0, 500, 3)), heavy_len=400)
     Bu = gen.random_csr(1, 1, 1.0, 0)  # placeholder for type
