@@ -163,6 +163,27 @@ class ClockSampler:
 # our implementation
 # ---------------------------------------------------------------------------
 
+# DRAM bytes (read + write) per intermediate product of the dense accumulation
+# kernels, from one ncu capture of the kernel as it stands (row sample 1 in
+# 128 of the R-MAT scale 20 workload, right operand and L2 pressure as in the
+# full case; summary and command in profiles/dense_tiers_rmat20_rows1in128.md).
+# Scaled by the full workload's products of the tier to give the per-launch
+# traffic; a kernel changed since its capture must drop out of this table.
+DRAM_BYTES_PER_PRODUCT = {"num_dense64": (809.343744e6 + 338.259e6) / 256228740}
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks of the default process group (the job's
+    time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def tier_work(plan, A_host, ip, nnz):
     """Rows, products and compulsory bytes of each row tier of the allocation
     and accumulation phases of A*A, following the library's tier rules (used
@@ -473,10 +494,7 @@ def run_ours(args):
     plan.profile(False)
     for ws in (ws_aa, ws_sa, ws_ts):
         plan.check_status(ws, "timed steps")
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     ms_step = ms / args.steps
     value = 2.0 * ip_step * world / (ms_step / 1e3) / 1e9
 
@@ -499,8 +517,14 @@ def run_ours(args):
         # its measured device time per step (= bytes per launch / mean launch time)
         bytes_step = work[top_name]["bytes"]
         achieved = bytes_step / (top_ms / args.steps / 1e3) / 1e9
+        traffic = None
+        if top_name in DRAM_BYTES_PER_PRODUCT and top_n > 0:
+            traffic = int(DRAM_BYTES_PER_PRODUCT[top_name] * work[top_name]["ip"]
+                          / (top_n / args.steps))
         roof = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak_gbs,
-                "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": None,
+                "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": traffic,
+                "traffic_source": "ncu dram bytes per product (small case) x products"
+                                  if traffic is not None else None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "launches_per_step": top_n / args.steps,
                 "bytes_per_step": int(bytes_step),
@@ -549,10 +573,7 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(ems, dev)
         e2e = {"value": 2.0 * ip_step * world / (ems / args.steps / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "note": "inputs copied from pinned host memory each step; C(S^T A S) and the "

@@ -28,9 +28,12 @@
  *   or by spgemm_status(). Kernels never fault or trap on bad input: they
  *   skip the offending access and record the condition.
  * - Value tolerance: every C value is within 1e-5 * sum_k |a_ik||b_kj| of
- *   the exact result. Rows whose output entries can gather more than
- *   opts.fp32_max_terms products accumulate in fp64 (the fp32 summation
- *   bound gamma_t = t*2^-24 stays below 1e-5 only for t <= 167).
+ *   the exact result. A plain fp32 sum of t products is only guaranteed
+ *   within gamma_t = t*2^-24 of that scale, below 1e-5 for t <= 167
+ *   (opts.fp32_max_terms). Entries that can gather more products (rows with
+ *   more than fp32_max_terms A entries, on columns of B with more than
+ *   fp32_max_terms entries) are summed in fp64, or as fp32 partial sums of
+ *   at most 128 terms added together in fp64.
  */
 #ifndef SPGEMM_H
 #define SPGEMM_H

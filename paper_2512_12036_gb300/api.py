@@ -318,6 +318,28 @@ class Plan:
         return blocks, ip_total, nnz_total
 
 
+def partition_rows(ip_row, parts: int):
+    """Contiguous row ranges [(r0, r1), ...], one per part (a rank), that cut
+    the prefix sums of the per-row intermediate products (Alg. 1) as evenly
+    as contiguous ranges allow: part p ends at the first row where the
+    prefix reaches (p+1)/parts of the total. Rows of C are independent, so
+    each rank multiplies its range of A by the whole of B with no exchange."""
+    ip = np.asarray(ip_row.cpu() if isinstance(ip_row, torch.Tensor) else ip_row,
+                    dtype=np.int64)
+    if parts < 1:
+        raise ValueError("parts must be >= 1")
+    n = ip.shape[0]
+    csum = np.cumsum(ip)
+    total = int(csum[-1]) if n else 0
+    cuts = [0]
+    for p in range(1, parts):
+        target = (total * p + parts - 1) // parts
+        r = int(np.searchsorted(csum, target, side="left")) + 1 if total else (n * p) // parts
+        cuts.append(min(max(r, cuts[-1]), n))
+    cuts.append(n)
+    return [(cuts[p], cuts[p + 1]) for p in range(parts)]
+
+
 def split_rows(row_nnz: torch.Tensor, max_block_nnz: int):
     """Consecutive row ranges whose nnz sums stay <= max_block_nnz (host-side
     planning from the per-row counts of the allocation phase)."""

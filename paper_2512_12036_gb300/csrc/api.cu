@@ -66,6 +66,14 @@ WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols) {
     return w;
 }
 
+void allow_max_dynamic_smem(const void* f, const spgemm_plan* p) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) return;
+    const size_t st = fa.sharedSizeBytes;
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         p->smem_optin > st ? (int)(p->smem_optin - st) : 0);
+}
+
 void init_occupancy(spgemm_plan* p) {
     occupancy_symbolic(p);
     occupancy_numeric(p);

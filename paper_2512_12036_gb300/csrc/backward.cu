@@ -298,14 +298,10 @@ __global__ void __launch_bounds__(kBwdBlockThreads) k_bwd_panel(BwdArgs x, int b
 // ---------------------------------------------------------------------------
 
 void occupancy_backward(spgemm_plan* p) {
-    cudaFuncSetAttribute(k_bwd_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kBwdWarps * kBwdDenseCols * 4);
-    cudaFuncSetAttribute(k_bwd_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kBwdWarps * kBwdWarpSlots * 8);
-    cudaFuncSetAttribute(k_bwd_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kBwdBlockSlots * 8);
-    cudaFuncSetAttribute(k_bwd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdPanel * 4);
-    (void)p;
+    allow_max_dynamic_smem((const void*)k_bwd_dense, p);
+    allow_max_dynamic_smem((const void*)k_bwd_warp, p);
+    allow_max_dynamic_smem((const void*)k_bwd_block, p);
+    allow_max_dynamic_smem((const void*)k_bwd_panel, p);
 }
 
 size_t backward_extra_bytes(long long a_nnz, long long b_nnz) {

@@ -22,14 +22,44 @@ __global__ void k_fill_i32(int* p, long long n, int v) {
         p[i] = v;
 }
 
+// Entries per column. Few columns (<= kColSmem): a shared-memory histogram
+// per block, added to cnt once per block (B = a narrow feature matrix puts
+// millions of entries on each column). Otherwise lanes of a warp that hold
+// the same column add their count with one atomic.
+constexpr int kColSmem = 8192;
+
+__global__ void k_colcount_smem(CsrDev B, int* cnt) {
+    __shared__ int h[kColSmem];
+    for (int i = threadIdx.x; i < B.cols; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const long long J0 = B.rows > 0 ? B.rpt[0] : 0;
+    const long long J1 = B.rows > 0 ? B.rpt[B.rows] : 0;
+    if (J0 >= 0 && J1 >= J0 && J1 <= B.nnz) {
+        for (long long j = J0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; j < J1;
+             j += (long long)gridDim.x * blockDim.x) {
+            const int c = B.col[j];
+            if ((unsigned)c < (unsigned)B.cols) atomicAdd(&h[c], 1);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < B.cols; i += blockDim.x)
+        if (h[i]) atomicAdd(&cnt[i], h[i]);
+}
+
 __global__ void k_colcount(CsrDev B, int* cnt) {
     const long long J0 = B.rows > 0 ? B.rpt[0] : 0;
     const long long J1 = B.rows > 0 ? B.rpt[B.rows] : 0;
     if (J0 < 0 || J1 < J0 || J1 > B.nnz) return;
-    for (long long j = J0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; j < J1;
-         j += (long long)gridDim.x * blockDim.x) {
-        const int c = B.col[j];
-        if ((unsigned)c < (unsigned)B.cols) atomicAdd(&cnt[c], 1);
+    const int lane = lane_id();
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    // warp-uniform trip count: all 32 lanes take part in every match
+    for (long long base = J0 + warp * 32; base < J1; base += nwarps * 32) {
+        const long long j = base + lane;
+        const int c = j < J1 ? B.col[j] : -1;
+        const bool ok = (unsigned)c < (unsigned)B.cols;
+        const unsigned peers = __match_any_sync(kFull, ok ? c : -1);
+        if (ok && lane == __ffs(peers) - 1) atomicAdd(&cnt[c], __popc(peers));
     }
 }
 
@@ -54,10 +84,17 @@ __global__ void k_bhot(CsrDev B, const int* flag, const int* rank, int* bhot) {
 }
 
 void launch_hot(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaStream_t s) {
-    if (!w.colcnt || B.cols <= 0) return;
+    // only rows with more than block_max_nnz entries (so B.cols > block_max_nnz)
+    // reach the fp64 dense tier, the one reader of these tables
+    if (!w.colcnt || B.cols <= 0 || B.cols <= p->opts.block_max_nnz) return;
     const int grid = p->num_sms * 8;
     SPG_LAUNCH(p, K_HOT, s, k_fill_i32<<<grid, 256, 0, s>>>(w.colcnt, (long long)B.cols + 1, 0));
-    if (B.nnz > 0) SPG_LAUNCH(p, K_HOT, s, k_colcount<<<grid, 256, 0, s>>>(B, w.colcnt));
+    if (B.nnz > 0) {
+        if (B.cols <= kColSmem)
+            SPG_LAUNCH(p, K_HOT, s, k_colcount_smem<<<grid, 256, 0, s>>>(B, w.colcnt));
+        else
+            SPG_LAUNCH(p, K_HOT, s, k_colcount<<<grid, 256, 0, s>>>(B, w.colcnt));
+    }
     SPG_LAUNCH(p, K_HOT, s, k_hot_flags<<<grid, 256, 0, s>>>(w.colcnt, B.cols, p->opts.fp32_max_terms));
     launch_row_ptr(p, w.colcnt, B.cols, w, w.hot_rank, s);
     SPG_LAUNCH(p, K_HOT, s, k_hot_cols<<<grid, 256, 0, s>>>(w.colcnt, w.hot_rank, B.cols, w.hot_col));

@@ -158,6 +158,12 @@ void launch_mcl_step(const spgemm_plan* p, const CsrDev& E, float theta, int k, 
                      cudaStream_t s);
 
 void init_occupancy(spgemm_plan* p);
+// Lets kernel f take as much dynamic shared memory as the device allows
+// beside f's static arrays. The limit is a per-kernel, process-wide
+// attribute, so plans with different table sizes must not set it to their
+// own request (a later plan with smaller tables would lower it under an
+// earlier plan's launches); each plan's occupancy uses its actual request.
+void allow_max_dynamic_smem(const void* f, const spgemm_plan* p);
 
 void prof_begin(const spgemm_plan* p, int kid, cudaStream_t s);
 void prof_end(const spgemm_plan* p, int kid, cudaStream_t s);

@@ -942,7 +942,7 @@ void occupancy_numeric(spgemm_plan* p) {
         {(const void*)k_num_dense_hot, kHotThreads, num_dense_hot_smem(p), &p->occ_num_dense_hot},
     };
     for (auto& k : ks) {
-        cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+        allow_max_dynamic_smem(k.f, p);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(k.occ, k.f, k.threads, k.smem);
         if (*k.occ < 1) *k.occ = 1;
     }

@@ -211,9 +211,9 @@ void occupancy_symbolic(spgemm_plan* p) {
     const size_t sw = (size_t)kWarpsPerBlockSW * kWarpTableSym * 4;
     const size_t sb = (size_t)pow2_ceil(2u * (unsigned)p->opts.block_max_ip) * 4;
     const size_t sd = sym_dense_smem(p);
-    cudaFuncSetAttribute(k_sym_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw);
-    cudaFuncSetAttribute(k_sym_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-    cudaFuncSetAttribute(k_sym_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
+    allow_max_dynamic_smem((const void*)k_sym_warp, p);
+    allow_max_dynamic_smem((const void*)k_sym_block, p);
+    allow_max_dynamic_smem((const void*)k_sym_dense, p);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_warp, k_sym_warp,
                                                   kWarpsPerBlockSW * 32, sw);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block, k_sym_block,

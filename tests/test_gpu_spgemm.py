@@ -197,6 +197,40 @@ def test_block_tier_clustered_columns(plan):
     check_product(plan, A, B)
 
 
+def test_dense_tier_narrow_b_hot_columns():
+    # a lower block-tier limit (2048) lets rows of a 5000-column B reach the
+    # fp64 dense tier; its hot-column counts then come from the per-block
+    # shared-memory histogram used for narrow B
+    rng = np.random.default_rng(61)
+    rows, cols = 1000, 5000
+    r, c = [], []
+    for k in range(rows):
+        cc = np.unique(np.concatenate([rng.choice(cols, size=30, replace=False), [7, 4000]]))
+        r.append(np.full(cc.size, k))
+        c.append(cc)
+    r, c = np.concatenate(r), np.concatenate(c)
+    B = gen.csr_from_coo(rows, cols, r, c, gen.uniform_open_closed(rng, r.size))
+    A = hub_matrix(20, rows, 62, heavy_rows={0, 5, 19}, heavy_len=400)
+    nnz = oracle.symbolic(A, B)
+    assert nnz.max() > 2048 and (np.bincount(B.col, minlength=cols) > 167).sum() >= 2
+    check_product(Plan(block_max_nnz=2048), A, B)
+
+
+def test_plans_with_different_tables_interleave(plan):
+    # kernel shared-memory limits are process-wide: a plan with smaller
+    # tables created later must not break the launches of an earlier plan
+    A = gen.random_csr(200, 300, 0.1, seed=71)
+    B = gen.random_csr(300, 100000, 0.002, seed=72)
+    nnz = oracle.symbolic(A, B)
+    assert nnz.max() > 4096 and nnz.max() <= 8192
+    small = Plan(block_max_nnz=2048, block_max_ip=4096)
+    check_product(plan, A, B)
+    check_product(small, A, B)
+    check_product(plan, A, B)
+    del small
+    check_product(plan, A, B)
+
+
 def test_dense_tier_unsorted_b(plan):
     B = hub_matrix(500, 50000, 7, heavy_rows=set(range(0, 500, 3)), heavy_len=400)
     Bu = gen.random_csr(1, 1, 1.0, 0)  # placeholder for type
