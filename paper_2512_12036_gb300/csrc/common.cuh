@@ -269,9 +269,215 @@ template <int kT, typename Acc>
 struct ExpandTile {
     long long off[kT + 1];        // exclusive prefix of segment lengths (non-empty entries)
     int bs[kT];                   // segment start in B
+    int ln[kT];                   // segment length (padded expansion)
     Acc a[kT];                    // a_ik (accumulation phase only)
     unsigned long long scratch[33];
 };
+
+// Position (0..31) of the (k+1)-th set bit of w, k < popc(w): a binary
+// search on the popcounts of the low halves.
+__device__ __forceinline__ int select_bit(unsigned w, int k) {
+    int bit = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int c = __popc(w & ((1u << s) - 1u));
+        if (k >= c) {
+            w >>= s;
+            bit += s;
+            k -= c;
+        }
+    }
+    return bit;
+}
+
+// Block-wide ordered emit of an occupancy bitmap: the set bits of words
+// [w0, w1) of bm (bit b of word w = column c0 + 32*w + b; bits outside the
+// range to emit must be clear) become entries (column, take(32*w + b)) at
+// positions written, written+1, ... of a row
+// that starts at colC/valC + out and holds nnz_row entries. Each warp owns a
+// contiguous run of words; a block scan of the warps' counts places the
+// runs; inside a run, 32 words at a time, entry s of the group goes to lane
+// s mod 32, which finds its word by a search on the warp prefix of the
+// popcounts and its bit by select_bit, so the column and value stores of a
+// warp are contiguous. take(kk) returns the value and clears its slot; the
+// words are cleared. Returns the number of entries. scratch holds 33 ints;
+// ends with a block barrier.
+template <int kT, class Take>
+__device__ __forceinline__ int emit_bitmap(unsigned* bm, int w0, int w1, int c0, int* colC,
+                                           float* valC, long long out, int written,
+                                           int nnz_row, int* scratch, Take&& take) {
+    constexpr int kWarps = kT / 32;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int nw = w1 - w0;
+    const int per = (nw + kWarps - 1) / kWarps;
+    const int ws = w0 + warp * per;
+    const int we = ws + per < w1 ? ws + per : w1;
+    int cnt = 0;
+    for (int g = ws; g < we; g += 32) cnt += g + lane < we ? __popc(bm[g + lane]) : 0;
+    cnt = warp_sum(cnt);
+    if (lane == 0) scratch[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        const int v = lane < kWarps ? scratch[lane] : 0;
+        const int inc = warp_incl_scan(v);
+        __syncwarp();
+        scratch[lane] = inc - v;
+        if (lane == 31) scratch[32] = inc;
+    }
+    __syncthreads();
+    int pos = written + scratch[warp];
+    const int total = scratch[32];
+    for (int g = ws; g < we; g += 32) {
+        const unsigned word = g + lane < we ? bm[g + lane] : 0u;
+        const int c = __popc(word);
+        const int inc = warp_incl_scan(c);
+        const int excl = inc - c;
+        const int T = __shfl_sync(kFull, inc, 31);
+        for (int r = 0; r < T; r += 32) {
+            const int p = r + lane;
+            const int src = warp_find_src(excl, p < T ? p : T - 1);
+            const unsigned sw = __shfl_sync(kFull, word, src);
+            const int se = __shfl_sync(kFull, excl, src);
+            if (p < T) {
+                const int kk = (g + src) * 32 + select_bit(sw, p - se);
+                const float v = take(kk);
+                const int o = pos + p;
+                if (o < nnz_row) {
+                    colC[out + o] = c0 + kk;
+                    valC[out + o] = v;
+                }
+            }
+        }
+        if (g + lane < we) bm[g + lane] = 0u;
+        pos += T;
+    }
+    __syncthreads();
+    return total;
+}
+
+// Per-thread form of emit_bitmap for sparse bitmaps (a few bits per word):
+// thread t owns consecutive words, a block scan of the popcounts places its
+// entries and it writes them in column order. Fewer instructions than the
+// warp-cooperative form when words hold few bits, at the price of scattered
+// stores. Same arguments and result; ends with a block barrier.
+template <int kT, class Take>
+__device__ __forceinline__ int emit_bitmap_lanes(unsigned* bm, int w0, int w1, int c0, int* colC,
+                                                 float* valC, long long out, int written,
+                                                 int nnz_row, int* scratch, Take&& take) {
+    const int wpt = (w1 - w0 + kT - 1) / kT;
+    const int wb = w0 + (int)threadIdx.x * wpt;
+    int cnt = 0;
+    for (int q = 0; q < wpt; ++q)
+        if (wb + q < w1) cnt += __popc(bm[wb + q]);
+    int tot;
+    int pos = written + block_excl_scan(cnt, scratch, &tot);
+    for (int q = 0; q < wpt; ++q) {
+        const int w = wb + q;
+        if (w >= w1) break;
+        unsigned bits = bm[w];
+        while (bits) {
+            const int kk = w * 32 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            const float v = take(kk);
+            if (pos < nnz_row) {
+                colC[out + pos] = c0 + kk;
+                valC[out + pos] = v;
+            }
+            ++pos;
+        }
+        bm[w] = 0u;
+    }
+    __syncthreads();
+    return tot;
+}
+
+// The per-warp walk of expand_tile over the compacted segments (offsets
+// off[0..nE], starts sbs[], multipliers sa[]). Off is int when the tile's
+// total fits 31 bits (the common case; fewer instructions per step), else
+// long long.
+template <typename Off, int kWarps, typename Acc, int kUnroll, bool kSeg, class Load, class Apply>
+__device__ __forceinline__ void expand_walk(const Off* off, const int* sbsv, const Acc* sav, int nE,
+                                            Off P, Load& load, Apply& apply) {
+    using Item = decltype(load(0));
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const Off per = ((P + Off(32) * kWarps - 1) / (Off(32) * kWarps)) * Off(32);
+    Off base = (Off)warp * per;
+    const Off wend = base + per < P ? base + per : P;
+    if (base >= wend) return;
+    // segment holding product `base`: largest e with off[e] <= base
+    int lo = 0, hi = nE - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= base) lo = mid;
+        else hi = mid - 1;
+    }
+    int s = lo;
+    Off so = off[s], se = off[s + 1];
+    int sbs = sbsv[s];
+    Acc sa = sav[s];
+    while (base < wend) {
+        int tq[kUnroll];
+        Acc aq[kUnroll];
+        bool vq[kUnroll];
+        int sq[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            vq[u] = false;
+            tq[u] = 0;
+            aq[u] = Acc(0);
+            sq[u] = 0;
+            if (base < wend) {                       // warp-uniform
+                if (base + 32 <= se) {               // the 32 products lie in segment s
+                    tq[u] = sbs + (int)(base - so) + lane;
+                    aq[u] = sa;
+                    sq[u] = s;
+                    vq[u] = base + lane < wend;
+                    base += 32;
+                    if (base == se && s + 1 < nE) {
+                        ++s;
+                        so = se;
+                        se = off[s + 1];
+                        sbs = sbsv[s];
+                        sa = sav[s];
+                    }
+                } else {
+                    const int e = s + lane;
+                    Off d = e <= nE ? off[e] - base : Off(1 << 30);
+                    if (d > Off(1 << 30)) d = Off(1 << 30);
+                    const int rel = (int)d;      // lane 0: <= 0, then non-decreasing
+                    const int wbs = e < nE ? sbsv[e] : 0;
+                    const Acc wa = e < nE ? sav[e] : Acc(0);
+                    const int src = warp_find_src(rel, lane);
+                    tq[u] = __shfl_sync(kFull, wbs, src) + (lane - __shfl_sync(kFull, rel, src));
+                    aq[u] = __shfl_sync(kFull, wa, src);
+                    sq[u] = s + src;
+                    vq[u] = base + lane < wend;
+                    // segment of base + 32
+                    const int cnt = __popc(__ballot_sync(kFull, rel <= 32));
+                    int ns = s + cnt - 1;
+                    if (cnt == 32 && s + 32 <= nE && off[s + 32] <= base + 32) ns = s + 32;
+                    s = ns < nE - 1 ? ns : nE - 1;
+                    base += 32;
+                    so = off[s];
+                    se = off[s + 1];
+                    sbs = sbsv[s];
+                    sa = sav[s];
+                }
+            }
+        }
+        Item it[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (vq[u]) it[u] = load(tq[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (vq[u]) {
+                if constexpr (kSeg) apply(it[u], aq[u], sq[u]);
+                else apply(it[u], aq[u]);
+            }
+        }
+    }
+}
 
 // Block-wide, load-balanced expansion of the products of one tile of A
 // entries. Every thread of the block calls it with the B segment
@@ -292,101 +498,130 @@ struct ExpandTile {
 template <int kT, typename Acc, int kUnroll, bool kSeg = false, class Load, class Apply>
 __device__ __forceinline__ void expand_tile(ExpandTile<kT, Acc>& sm, int bs, int len, Acc a,
                                             Load&& load, Apply&& apply) {
-    using Item = decltype(load(0));
-    const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const int tid = threadIdx.x;
     constexpr int kWarps = kT / 32;
     constexpr unsigned long long kMask48 = (1ull << 48) - 1ull;
     const unsigned long long v = len > 0 ? ((1ull << 48) | (unsigned long long)len) : 0ull;
     unsigned long long tot;
     const unsigned long long ex = block_excl_scan_u64(v, sm.scratch, &tot);
+    const int nE = (int)(tot >> 48);
+    const long long P = (long long)(tot & kMask48);
+    const bool narrow = P < (1ll << 30);             // block-uniform
+    int* off32 = reinterpret_cast<int*>(sm.off);     // same storage, int view
+    if (len > 0) {
+        const int ci = (int)(ex >> 48);
+        if (narrow) off32[ci] = (int)(ex & kMask48);
+        else sm.off[ci] = (long long)(ex & kMask48);
+        sm.bs[ci] = bs;
+        sm.a[ci] = a;
+    }
+    if (tid == 0) {
+        if (narrow) off32[nE] = (int)P;
+        else sm.off[nE] = P;
+    }
+    __syncthreads();
+    if (narrow)
+        expand_walk<int, kWarps, Acc, kUnroll, kSeg>(off32, sm.bs, sm.a, nE, (int)P, load, apply);
+    else
+        expand_walk<long long, kWarps, Acc, kUnroll, kSeg>(sm.off, sm.bs, sm.a, nE, P, load, apply);
+    __syncthreads();
+}
+
+// expand_tile with every segment padded to a multiple of 32 products in the
+// flattened order: the warps' equal ranges are 32-aligned, so each 32-product
+// step of a warp lies inside one segment and lane l takes position
+// bs + offset + l when that is below the segment's length (lanes in the
+// padding idle). Moving on to the next segment is a constant-time step and
+// no step needs a segment search, which suits tiles whose segments are
+// mostly long (in R-MAT heavy rows about 9 in 10 lanes stay busy). Same
+// contract as expand_tile, including kSeg.
+template <typename Off, int kWarps, typename Acc, int kUnroll, bool kSeg, class Load, class Apply>
+__device__ __forceinline__ void expand_walk_padded(const Off* off, const int* sbsv, const int* slnv,
+                                                   const Acc* sav, int nE, Off P, Load& load,
+                                                   Apply& apply) {
+    using Item = decltype(load(0));
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const Off per = ((P / 32 + kWarps - 1) / kWarps) * 32;
+    Off base = (Off)warp * per;
+    const Off wend = base + per < P ? base + per : P;
+    if (base >= wend) return;
+    int lo = 0, hi = nE - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= base) lo = mid;
+        else hi = mid - 1;
+    }
+    int s = lo;
+    Off so = off[s], se = off[s + 1];
+    int sbs = sbsv[s], sln = slnv[s];
+    Acc sa = sav[s];
+    while (base < wend) {
+        int tq[kUnroll];
+        Acc aq[kUnroll];
+        bool vq[kUnroll];
+        int sq[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            vq[u] = false;
+            tq[u] = 0;
+            aq[u] = Acc(0);
+            sq[u] = 0;
+            if (base < wend) {                       // warp-uniform
+                if (base >= se) {                    // next segment (padded length >= 32)
+                    ++s;
+                    so = se;
+                    se = off[s + 1];
+                    sbs = sbsv[s];
+                    sln = slnv[s];
+                    sa = sav[s];
+                }
+                const int o = (int)(base - so) + lane;
+                tq[u] = sbs + o;
+                aq[u] = sa;
+                sq[u] = s;
+                vq[u] = o < sln;
+                base += 32;
+            }
+        }
+        Item it[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (vq[u]) it[u] = load(tq[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (vq[u]) {
+                if constexpr (kSeg) apply(it[u], aq[u], sq[u]);
+                else apply(it[u], aq[u]);
+            }
+        }
+    }
+}
+
+template <int kT, typename Acc, int kUnroll, bool kSeg = false, class Load, class Apply>
+__device__ __forceinline__ void expand_tile_padded(ExpandTile<kT, Acc>& sm, int bs, int len, Acc a,
+                                                   Load&& load, Apply&& apply) {
+    const int tid = threadIdx.x;
+    constexpr int kWarps = kT / 32;
+    constexpr unsigned long long kMask48 = (1ull << 48) - 1ull;
+    const unsigned long long plen = (unsigned long long)(((long long)len + 31) & ~31ll);
+    const unsigned long long v = len > 0 ? ((1ull << 48) | plen) : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_excl_scan_u64(v, sm.scratch, &tot);
+    const int nE = (int)(tot >> 48);
+    const long long P = (long long)(tot & kMask48);    // a multiple of 32
     if (len > 0) {
         const int ci = (int)(ex >> 48);
         sm.off[ci] = (long long)(ex & kMask48);
         sm.bs[ci] = bs;
+        sm.ln[ci] = len;
         sm.a[ci] = a;
     }
-    const int nE = (int)(tot >> 48);
-    const long long P = (long long)(tot & kMask48);
     if (tid == 0) sm.off[nE] = P;
     __syncthreads();
-    const long long per = ((P + 32ll * kWarps - 1) / (32ll * kWarps)) * 32ll;
-    long long base = (long long)warp * per;
-    const long long wend = base + per < P ? base + per : P;
-    if (base < wend) {
-        // segment holding product `base`: largest e with off[e] <= base
-        int lo = 0, hi = nE - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sm.off[mid] <= base) lo = mid;
-            else hi = mid - 1;
-        }
-        int s = lo;
-        long long so = sm.off[s], se = sm.off[s + 1];
-        int sbs = sm.bs[s];
-        Acc sa = sm.a[s];
-        while (base < wend) {
-            int tq[kUnroll];
-            Acc aq[kUnroll];
-            bool vq[kUnroll];
-            int sq[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                vq[u] = false;
-                tq[u] = 0;
-                aq[u] = Acc(0);
-                sq[u] = 0;
-                if (base < wend) {                       // warp-uniform
-                    if (base + 32 <= se) {               // the 32 products lie in segment s
-                        tq[u] = sbs + (int)(base - so) + lane;
-                        aq[u] = sa;
-                        sq[u] = s;
-                        vq[u] = base + lane < wend;
-                        base += 32;
-                        if (base == se && s + 1 < nE) {
-                            ++s;
-                            so = se;
-                            se = sm.off[s + 1];
-                            sbs = sm.bs[s];
-                            sa = sm.a[s];
-                        }
-                    } else {
-                        const int e = s + lane;
-                        long long d = e <= nE ? sm.off[e] - base : (1ll << 30);
-                        if (d > (1ll << 30)) d = 1ll << 30;
-                        const int rel = (int)d;      // lane 0: <= 0, then non-decreasing
-                        const int wbs = e < nE ? sm.bs[e] : 0;
-                        const Acc wa = e < nE ? sm.a[e] : Acc(0);
-                        const int src = warp_find_src(rel, lane);
-                        tq[u] = __shfl_sync(kFull, wbs, src) + (lane - __shfl_sync(kFull, rel, src));
-                        aq[u] = __shfl_sync(kFull, wa, src);
-                        sq[u] = s + src;
-                        vq[u] = base + lane < wend;
-                        // segment of base + 32
-                        const int cnt = __popc(__ballot_sync(kFull, rel <= 32));
-                        int ns = s + cnt - 1;
-                        if (cnt == 32 && s + 32 <= nE && sm.off[s + 32] <= base + 32) ns = s + 32;
-                        s = ns < nE - 1 ? ns : nE - 1;
-                        base += 32;
-                        so = sm.off[s];
-                        se = sm.off[s + 1];
-                        sbs = sm.bs[s];
-                        sa = sm.a[s];
-                    }
-                }
-            }
-            Item it[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                if (vq[u]) it[u] = load(tq[u]);
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                if (vq[u]) {
-                    if constexpr (kSeg) apply(it[u], aq[u], sq[u]);
-                    else apply(it[u], aq[u]);
-                }
-            }
-        }
-    }
+    // one 64-bit walk: a second, 32-bit instantiation here pushed the fp32
+    // dense kernel past 64 registers (spills, 16% slower)
+    expand_walk_padded<long long, kWarps, Acc, kUnroll, kSeg>(sm.off, sm.bs, sm.ln, sm.a, nE, P,
+                                                              load, apply);
     __syncthreads();
 }
 

@@ -445,6 +445,12 @@ constexpr int kGroup = 160;
 #ifndef SPG_D32_UNROLL
 #define SPG_D32_UNROLL 4
 #endif
+#ifndef SPG_PAD_D32
+#define SPG_PAD_D32 1
+#endif
+#ifndef SPG_PAD_HOT
+#define SPG_PAD_HOT 0
+#endif
 #ifndef SPG_D32_THREADS
 #define SPG_D32_THREADS 1024
 #endif
@@ -570,7 +576,12 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                     }
                 }
                 if (kMode == 0) {
-                    expand_tile<kNumDenseThreads, float, SPG_D32_UNROLL>(tile, bs, len, mya, load, apply);
+                    if (SPG_PAD_D32)
+                        expand_tile_padded<kNumDenseThreads, float, SPG_D32_UNROLL>(tile, bs, len, mya,
+                                                                                   load, apply);
+                    else
+                        expand_tile<kNumDenseThreads, float, SPG_D32_UNROLL>(tile, bs, len, mya, load,
+                                                                            apply);
                 } else {
                     for (int g0 = 0; g0 < na; g0 += kGroup) {
                         const bool mine = (int)threadIdx.x >= g0 && (int)threadIdx.x < g0 + kGroup;
@@ -602,24 +613,17 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                             }
                         }
                     }
-                    expand_tile<kNumDenseThreads, float, 4>(tile, bs, len, a, load, apply);
+                    if (SPG_PAD_D32 && kMode == 0)
+                        expand_tile_padded<kNumDenseThreads, float, 4>(tile, bs, len, a, load, apply);
+                    else
+                        expand_tile<kNumDenseThreads, float, 4>(tile, bs, len, a, load, apply);
                     if (kMode == 1) flush();
                 }
             }
-            // emit this pass in column order: thread t owns words [w0, w0+wpt)
+            // emit this pass in column order
             const int nw = (span + 31) >> 5;
-            int cnt = 0;
-            for (int q = 0; q < wpt; ++q)
-                if (w0 + q < nw) cnt += __popc(bm[w0 + q]);
-            int tot;
-            int pos = written + block_excl_scan(cnt, scratch, &tot);
-            for (int q = 0; q < wpt; ++q) {
-                const int w = w0 + q;
-                if (w >= nw) break;
-                unsigned wbits = bm[w];
-                while (wbits) {
-                    const int kk = w * 32 + __ffs(wbits) - 1;
-                    wbits &= wbits - 1;
+            written += emit_bitmap_lanes<kNumDenseThreads>(
+                bm, 0, nw, c0, colC, valC, out, written, nnz_row, scratch, [&](int kk) {
                     float v;
                     if (kMode == 1) {
                         v = (float)acc[kk];
@@ -628,16 +632,8 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                         v = st[kk];
                         st[kk] = 0.f;
                     }
-                    if (pos < nnz_row) {
-                        colC[out + pos] = c0 + kk;
-                        valC[out + pos] = v;
-                    }
-                    ++pos;
-                }
-                bm[w] = 0u;
-            }
-            written += tot;
-            __syncthreads();
+                    return v;
+                });
         }
         if (threadIdx.x == 0 && written != nnz_row) set_status(ctl, ST_INTERNAL);
     }
@@ -803,8 +799,12 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                     hi = pc1;
                 }
                 if (cached) {
-                    expand_tile<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, bs, len, mya, load,
-                                                                          apply);
+                    if (SPG_PAD_HOT)
+                        expand_tile_padded<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, bs, len, mya,
+                                                                                     load, apply);
+                    else
+                        expand_tile<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, bs, len, mya, load,
+                                                                              apply);
                     fold();
                 } else {
                     for (int tb = rs; tb < re; tb += kHotThreads) {
@@ -826,8 +826,12 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                                 }
                             }
                         }
-                        expand_tile<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, tbs, tlen, a,
-                                                                              load, apply);
+                        if (SPG_PAD_HOT)
+                            expand_tile_padded<kHotThreads, float, SPG_HOT_UNROLL, true>(
+                                tile, tbs, tlen, a, load, apply);
+                        else
+                            expand_tile<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, tbs, tlen, a,
+                                                                                  load, apply);
                         fold();
                     }
                 }
@@ -840,34 +844,13 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                 }
                 __syncthreads();
                 // emit [lo, hi) in column order (bits outside it are clear)
-                const int w0 = (lo - pc0) >> 5;
-                const int w1 = (hi - pc0 + 31) >> 5;
-                const int wpt = (w1 - w0 + kHotThreads - 1) / kHotThreads;
-                const int wb = w0 + t * wpt;
-                int cnt = 0;
-                for (int q = 0; q < wpt; ++q)
-                    if (wb + q < w1) cnt += __popc(bm[wb + q]);
-                int tot;
-                int pos = written + block_excl_scan(cnt, scratch, &tot);
-                for (int q = 0; q < wpt; ++q) {
-                    const int wq = wb + q;
-                    if (wq >= w1) break;
-                    unsigned wbits = bm[wq];
-                    while (wbits) {
-                        const int kk = wq * 32 + __ffs(wbits) - 1;
-                        wbits &= wbits - 1;
+                written += emit_bitmap<kHotThreads>(
+                    bm, (lo - pc0) >> 5, (hi - pc0 + 31) >> 5, pc0, colC, valC, out, written,
+                    nnz_row, scratch, [&](int kk) {
                         const float v = st[kk];
                         st[kk] = 0.f;
-                        if (pos < nnz_row) {
-                            colC[out + pos] = pc0 + kk;
-                            valC[out + pos] = v;
-                        }
-                        ++pos;
-                    }
-                    bm[wq] = 0u;
-                }
-                written += tot;
-                __syncthreads();
+                        return v;
+                    });
             }
             cur = nxt;
             nxt = nxt2;
@@ -910,6 +893,9 @@ void occupancy_numeric(spgemm_plan* p) {
         const size_t per = hot_smem_of(p->opts.panel_cols, 1) - hot_smem_of(p->opts.panel_cols, 0);
         p->hot_ppp = p->smem_optin > fixed + per ? (int)((p->smem_optin - fixed) / per) : 1;
         if (p->hot_ppp > 64) p->hot_ppp = 64;
+#ifdef SPG_HOT_PPP_CAP
+        if (p->hot_ppp > SPG_HOT_PPP_CAP) p->hot_ppp = SPG_HOT_PPP_CAP;
+#endif
     }
     // fp32 dense tier: as many table panels per pass as a block's share of
     // the SM's shared memory holds beside its static arrays
@@ -926,6 +912,9 @@ void occupancy_numeric(spgemm_plan* p) {
         const size_t per = 4 * (size_t)p->opts.panel_cols + p->opts.panel_cols / 8;
         p->d32_ppp = avail >= per ? (int)(avail / per) : 1;
         if (p->d32_ppp > 64) p->d32_ppp = 64;
+#ifdef SPG_D32_PPP_CAP
+        if (p->d32_ppp > SPG_D32_PPP_CAP) p->d32_ppp = SPG_D32_PPP_CAP;
+#endif
     }
     struct K {
         const void* f;
