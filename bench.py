@@ -169,7 +169,7 @@ class ClockSampler:
 # full case; summary and command in profiles/dense_tiers_rmat20_rows1in128.md).
 # Scaled by the full workload's products of the tier to give the per-launch
 # traffic; a kernel changed since its capture must drop out of this table.
-DRAM_BYTES_PER_PRODUCT = {"num_dense64": (809.343744e6 + 338.259e6) / 256228740}
+DRAM_BYTES_PER_PRODUCT = {"num_dense64": (793.911040e6 + 331.378e6) / 256228740}
 
 
 def max_over_ranks(x: float, device) -> float:

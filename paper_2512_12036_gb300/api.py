@@ -294,12 +294,15 @@ class Plan:
 
         Returns (blocks, ip_total, nnz_total) with blocks a list of
         (row_begin, row_end, DeviceCSR). ``out`` may give preallocated blocks
-        from an earlier call with the same operands."""
+        from an earlier call with the same operands (the same structure): the
+        call then reuses their row ranges and never waits for the device
+        (ip_total and nnz_total come back as None)."""
         if ws is None:
             ws = self.workspace(A, B)
-        ip_row, ip_total = self.count(A, B, ws, total=out is None, stream=stream)
-        row_nnz, nnz_total = self.symbolic(A, B, ip_row, ws, stream=stream)
-        bounds = split_rows(row_nnz, max_block_nnz)
+        fresh = out is None
+        ip_row, ip_total = self.count(A, B, ws, total=fresh, stream=stream)
+        row_nnz, nnz_total = self.symbolic(A, B, ip_row, ws, total=fresh, stream=stream)
+        bounds = split_rows(row_nnz, max_block_nnz) if fresh else [(r0, r1) for r0, r1, _ in out]
         blocks = []
         for q, (r0, r1) in enumerate(bounds):
             if out is not None:
@@ -342,7 +345,10 @@ def partition_rows(ip_row, parts: int):
 
 def split_rows(row_nnz: torch.Tensor, max_block_nnz: int):
     """Consecutive row ranges whose nnz sums stay <= max_block_nnz (host-side
-    planning from the per-row counts of the allocation phase)."""
+    planning from the per-row counts of the allocation phase). The fewest
+    blocks the limit allows, cut at even shares of the total so that no block
+    is a small remainder (a launch over a small block still waits for its
+    heaviest row); greedy filling where even cuts would break the limit."""
     counts = row_nnz.to(torch.int64).cpu().numpy()
     n = counts.shape[0]
     if n == 0:
@@ -350,6 +356,18 @@ def split_rows(row_nnz: torch.Tensor, max_block_nnz: int):
     if counts.max(initial=0) > max_block_nnz:
         raise ValueError("a single row exceeds the block limit")
     csum = np.cumsum(counts)
+    total = int(csum[-1])
+    nb = max(1, -(-total // max_block_nnz))
+    if nb > 1:
+        cuts = [0]
+        for q in range(1, nb):
+            r = int(np.searchsorted(csum, total * q / nb, side="left")) + 1
+            cuts.append(min(max(r, cuts[-1] + 1), n))
+        cuts.append(n)
+        bounds = [(a, b) for a, b in zip(cuts, cuts[1:]) if b > a]
+        sums = [int(csum[b - 1] - (csum[a - 1] if a else 0)) for a, b in bounds]
+        if max(sums) <= max_block_nnz:
+            return bounds
     bounds = []
     r0 = 0
     base = 0

@@ -92,8 +92,12 @@ def test_split_rows_respects_limit():
             assert a1 == b0 and a1 > a0
         sums = [int(counts[a:b].sum()) for a, b in bounds]
         assert max(sums) <= limit
-        # greedy: no block could take the next row
-        for (a, b), s in zip(bounds[:-1], sums):
-            assert s + int(counts[b]) > limit
+        # at least the fewest blocks the limit allows; exactly that many, cut
+        # evenly (no small remainder), whenever an even cut must fit
+        need = -(-int(counts.sum()) // limit)
+        assert len(bounds) >= need
+        if int(counts.sum()) / need + int(counts.max()) <= limit:
+            assert len(bounds) == need
+            assert min(sums) >= int(counts.sum()) / need - int(counts.max())
     with pytest.raises(ValueError):
         split_rows(counts, 10)
