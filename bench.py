@@ -266,6 +266,7 @@ def pattern_batched(num_graphs: int, device):
     e1.synchronize()
     ms_bwd = e0.elapsed_time(e1) / 3
     plan.check_status(ws_b, "batched backward")
+    layer = pattern_pruned_layer(A, plan, device)
     # plain per-request path over the same subgraphs (all arrive at t = 0)
     pplan = Plan(device=device.index)
     off = batch.node_off
@@ -291,9 +292,55 @@ def pattern_batched(num_graphs: int, device):
                         "forward_gflops": gflop / (ms_fwd / 1e3),
                         "p50_ms": ms_fwd, "p99_ms": ms_fwd, "launch": "one CUDA graph replay",
                         "autotuned_opts": opts, "candidates_ms": timings},
+            "pruned_gcn_layer": layer,
             "plain": {"total_ms": 1e3 * plain_s, "gflops": gflop / plain_s,
                       "p50_ms": 1e3 * _pct(done_at, 0.5), "p99_ms": 1e3 * _pct(done_at, 0.99)},
             "max_rel_diff_batched_vs_plain": max_rel}
+
+
+def pattern_pruned_layer(A, plan, device, d: int = 256, dout: int = 256, k: int = 32,
+                         reps: int = 3):
+    """One GCN layer with a top-k pruning layer (Eq. 1-3) on the batch graph:
+    X dense N(0,1) n x d (seeded), W d x dout; forward A*TopK(X,k)*W and its
+    backward (dX, dW), timed with CUDA events."""
+    import torch
+
+    from paper_2512_12036_gb300 import gnn
+
+    torch.backends.cuda.matmul.allow_tf32 = False
+    g = torch.Generator(device=device).manual_seed(7)
+    X = torch.randn(A.rows, d, generator=g, device=device).requires_grad_(True)
+    W = (torch.randn(d, dout, generator=g, device=device) / d ** 0.5).requires_grad_(True)
+    dY = torch.randn(A.rows, dout, generator=g, device=device)
+
+    def fwd():
+        return gnn.pruned_aggregation(A, X, W, k, plan)
+
+    Y = fwd()
+    Y.backward(dY)
+    torch.cuda.synchronize()
+    tf, tb = [], []
+    for _ in range(reps):
+        X.grad = None
+        W.grad = None
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        Y = fwd()
+        e1.record()
+        Y.backward(dY)
+        e2.record()
+        e2.synchronize()
+        tf.append(e0.elapsed_time(e1))
+        tb.append(e1.elapsed_time(e2))
+    ip = A.nnz * min(k, d)          # every row of TopK(X) holds min(k, d) entries
+    fwd_ms, bwd_ms = statistics.median(tf), statistics.median(tb)
+    dense_gflop = 2.0 * A.rows * d * dout / 1e9
+    return {"n": A.rows, "d": d, "dout": dout, "k": k, "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "spgemm_products": int(ip),
+            "forward_gflops_all": (2.0 * ip / 1e9 + dense_gflop) / (fwd_ms / 1e3),
+            "note": "forward: TopK, A*TopK(X) (hash SpGEMM), dense C*W (cuBLAS fp32); backward: "
+                    "dY*W^T and C^T*dY (cuBLAS), gather at C's pattern, spgemm_backward, "
+                    "scatter into dX (M_k-masked)"}
 
 
 def pattern_served(n_requests: int, device, A_big=None, S_big=None, St_big=None):

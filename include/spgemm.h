@@ -248,6 +248,41 @@ int spgemm_mcl_step(const spgemm_plan* plan, const spgemm_csr* E, float theta, i
                     int32_t order, void* ws, size_t ws_bytes, int32_t* row_ptr_out,
                     int32_t* col_out, float* val_out, int64_t* nnz_out, void* stream);
 
+/* --- Pruned GNN layer (Section IV-C, Eqs. 1-3): X_l = A * TopK(X_{l-1}, k) * W_l.
+ * The products with the dense W_l are plain dense GEMMs and are left to the
+ * caller (a BLAS); these three calls supply the sparse steps around the
+ * SpGEMM A * TopK(X) and its backward (spgemm_backward gives the gradient on
+ * TopK's pattern, i.e. M_k (.) (A^T dC) of Eq. 3). */
+
+/* TopK of Eq. 2 on each row of the dense row-major n x d matrix X (leading
+ * dimension ldx >= d, device): keeps the min(k, d) largest values of the
+ * row, the mask M_k and its values as CSR with row_ptr [n+1] (row i starts
+ * at i*min(k,d)), col / val [n*min(k,d)] in ascending column order (device,
+ * caller-allocated). Order: fp32 values by IEEE total order (a positive NaN
+ * ranks above +inf, a negative one below -inf); equal values go to the
+ * smaller column. Stored zeros count like any value. k = 0 gives empty rows.
+ * Errors: SPGEMM_ERR_INVALID (null pointers, k < 0, ldx < d),
+ * SPGEMM_ERR_OVERFLOW (n*min(k,d) beyond int32). Asynchronous. */
+int spgemm_topk_dense(const spgemm_plan* plan, const float* X, int32_t n, int32_t d, int64_t ldx,
+                      int32_t k, int32_t* row_ptr, int32_t* col, float* val, void* stream);
+
+/* X[i, j] += v for every entry (i, j) of M, v = vals[q] (or M->vals[q] when
+ * vals is NULL): M (.) applied to a gradient on M's pattern (Eq. 3) when X
+ * starts at zero. X: dense row-major M->rows x ldx (ldx >= M->cols, device).
+ * Repeated columns add up. ws: an initialised workspace (>= 1 KB, 256-byte
+ * aligned; its status word records out-of-range columns, which are
+ * skipped). Asynchronous. */
+int spgemm_csr_scatter_dense(const spgemm_plan* plan, const spgemm_csr* M, const float* vals,
+                             float* X, int64_t ldx, void* ws, size_t ws_bytes, void* stream);
+
+/* out[q] = D[i, j] for every entry q = (i, j) of M: a dense matrix read at
+ * M's pattern (the gradient of A * TopK(X), dY * W^T, is needed only where
+ * that product has entries). D: dense row-major M->rows x ldd (ldd >=
+ * M->cols, device); out [M->nnz] (device). ws as for the scatter; an
+ * out-of-range column gives 0 and records SPGEMM_ERR_INVALID. Asynchronous. */
+int spgemm_csr_gather_dense(const spgemm_plan* plan, const spgemm_csr* M, const float* D,
+                            int64_t ldd, float* out, void* ws, size_t ws_bytes, void* stream);
+
 /* Synchronise `stream`, read and clear the workspace's device status word;
  * *status receives the SPGEMM_ERR_* code it maps to (SPGEMM_OK if clean). */
 int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status);

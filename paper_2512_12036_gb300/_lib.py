@@ -71,6 +71,10 @@ PROTOTYPES = {
                                       c_i64, c_vp, c_vp]),
     "spgemm_mcl_step": (ctypes.c_int, [c_vp, _CSR, ctypes.c_float, c_i32, ctypes.c_float, c_i32,
                                        c_vp, c_sz, c_vp, c_vp, c_vp, _P(c_i64), c_vp]),
+    "spgemm_topk_dense": (ctypes.c_int, [c_vp, c_vp, c_i32, c_i32, c_i64, c_i32, c_vp, c_vp, c_vp,
+                                         c_vp]),
+    "spgemm_csr_scatter_dense": (ctypes.c_int, [c_vp, _CSR, c_vp, c_vp, c_i64, c_vp, c_sz, c_vp]),
+    "spgemm_csr_gather_dense": (ctypes.c_int, [c_vp, _CSR, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp]),
     "spgemm_status": (ctypes.c_int, [c_vp, c_vp, c_vp, _P(ctypes.c_int)]),
     "spgemm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "spgemm_profile_enable": (ctypes.c_int, [c_vp, ctypes.c_int]),

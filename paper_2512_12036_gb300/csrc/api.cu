@@ -84,7 +84,7 @@ const char* const kKernelNames[K_NUM_KERNELS] = {
     "fill", "check_rpt", "zero_total", "ip_count", "sum", "group_hist", "group_scan",
     "group_scatter", "scan_part", "scan_top", "scan_final", "reset_flag", "bpanel", "sym_esc",
     "sym_warp", "sym_block", "sym_dense", "num_esc", "num_warp32", "num_warp64", "num_block32",
-    "num_block64", "num_dense32", "num_dense64", "backward", "guard", "mcl", "hot"};
+    "num_block64", "num_dense32", "num_dense64", "backward", "guard", "mcl", "hot", "layer"};
 
 void prof_begin(const spgemm_plan* p, int kid, cudaStream_t s) {
     (void)kid;
@@ -536,6 +536,41 @@ int spgemm_mcl_step(const spgemm_plan* plan, const spgemm_csr* E, float theta, i
     if (rc) return rc;
     if (nnz_out) return sync_read(w.ctl, 2, nnz_out, s);
     return SPGEMM_OK;
+}
+
+int spgemm_topk_dense(const spgemm_plan* plan, const float* X, int32_t n, int32_t d, int64_t ldx,
+                      int32_t k, int32_t* row_ptr, int32_t* col, float* val, void* stream) {
+    if (!plan || n < 0 || d < 0 || k < 0 || ldx < d || !row_ptr) return SPGEMM_ERR_INVALID;
+    if (n > 0 && d > 0 && !X) return SPGEMM_ERR_INVALID;
+    const long long kk = k < d ? k : d;
+    if ((long long)n * kk > 2147483647ll) return SPGEMM_ERR_OVERFLOW;
+    if ((long long)n * kk > 0 && (!col || !val)) return SPGEMM_ERR_INVALID;
+    launch_topk(plan, X, n, d, (long long)ldx, k, row_ptr, col, val, (cudaStream_t)stream);
+    return cuda_err(cudaGetLastError());
+}
+
+int spgemm_csr_scatter_dense(const spgemm_plan* plan, const spgemm_csr* M, const float* vals,
+                             float* X, int64_t ldx, void* ws, size_t ws_bytes, void* stream) {
+    if (!plan) return SPGEMM_ERR_INVALID;
+    int rc = check_csr(M, vals == nullptr);
+    if (rc) return rc;
+    if (ldx < M->cols || (M->rows > 0 && M->cols > 0 && !X)) return SPGEMM_ERR_INVALID;
+    if (!ws || ws_bytes < sizeof(Ctl) || ((uintptr_t)ws & 255)) return SPGEMM_ERR_WORKSPACE;
+    launch_scatter_dense(plan, dev_view(M), vals ? vals : M->vals, X, (long long)ldx, (Ctl*)ws,
+                         (cudaStream_t)stream);
+    return cuda_err(cudaGetLastError());
+}
+
+int spgemm_csr_gather_dense(const spgemm_plan* plan, const spgemm_csr* M, const float* D,
+                            int64_t ldd, float* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!plan) return SPGEMM_ERR_INVALID;
+    int rc = check_csr(M, false);
+    if (rc) return rc;
+    if (ldd < M->cols || (M->rows > 0 && M->cols > 0 && !D) || (M->nnz > 0 && !out))
+        return SPGEMM_ERR_INVALID;
+    if (!ws || ws_bytes < sizeof(Ctl) || ((uintptr_t)ws & 255)) return SPGEMM_ERR_WORKSPACE;
+    launch_gather_dense(plan, dev_view(M), D, (long long)ldd, out, (Ctl*)ws, (cudaStream_t)stream);
+    return cuda_err(cudaGetLastError());
 }
 
 int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status) {

@@ -14,7 +14,7 @@ enum KernelId : int {
     K_FILL, K_CHECK_RPT, K_ZERO, K_IP_COUNT, K_SUM, K_GROUP_HIST, K_GROUP_SCAN, K_GROUP_SCATTER,
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_FINAL, K_RESET, K_BPANEL, K_SYM_ESC, K_SYM_WARP, K_SYM_BLOCK,
     K_SYM_DENSE, K_NUM_ESC, K_NUM_WARP32, K_NUM_WARP64, K_NUM_BLOCK32, K_NUM_BLOCK64,
-    K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_GUARD, K_MCL, K_HOT, K_NUM_KERNELS
+    K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_GUARD, K_MCL, K_HOT, K_LAYER, K_NUM_KERNELS
 };
 extern const char* const kKernelNames[K_NUM_KERNELS];
 
@@ -153,6 +153,12 @@ void launch_backward(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
                      const int* colC, const float* dC, float* dA, float* dB, const WsPtrs& w,
                      double* dB64, double* dA64, cudaStream_t s);
 size_t backward_extra_bytes(long long a_nnz, long long b_nnz);
+void launch_topk(const spgemm_plan* p, const float* X, int n, int d, long long ldx, int k,
+                 int* rpt, int* col, float* val, cudaStream_t s);
+void launch_scatter_dense(const spgemm_plan* p, const CsrDev& M, const float* vals, float* X,
+                          long long ldx, Ctl* ctl, cudaStream_t s);
+void launch_gather_dense(const spgemm_plan* p, const CsrDev& M, const float* D, long long ldd,
+                         float* out, Ctl* ctl, cudaStream_t s);
 void launch_mcl_step(const spgemm_plan* p, const CsrDev& E, float theta, int k, double r,
                      int order, const WsPtrs& w, int* rpt_out, int* col_out, float* val_out,
                      cudaStream_t s);
