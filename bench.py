@@ -343,6 +343,38 @@ def pattern_pruned_layer(A, plan, device, d: int = 256, dout: int = 256, k: int 
                     "scatter into dX (M_k-masked)"}
 
 
+def pattern_sampling(A, device, minibatches: int = 64, batch: int = 1024, fanouts=(25, 10),
+                     reps: int = 3):
+    """Bulk neighbourhood sampling (Section IV-C): `minibatches` minibatches of
+    `batch` vertices of the R-MAT graph stacked in one Q, fanouts per layer;
+    per layer P = Q*A, SAMPLE, column selection, EXTRACT = P*S. Uniform
+    (GraphSAGE) and squared-weight (LADIES-style) draws. Wall time per bulk
+    call (host syncs for the allocations included)."""
+    import torch
+
+    from paper_2512_12036_gb300 import Plan, sampling
+
+    plan = Plan(device=device.index)
+    rng = np.random.default_rng(12)
+    verts = np.concatenate([np.sort(rng.choice(A.rows, size=batch, replace=False))
+                            for _ in range(minibatches)])
+    out = {"minibatches": minibatches, "batch": batch, "fanouts": list(fanouts)}
+    for name, mode in (("uniform", sampling.UNIFORM), ("squared_weights", sampling.BY_SQUARE)):
+        sampling.sample_layers(A, verts, fanouts, plan, mode=mode, seed=0)
+        torch.cuda.synchronize()
+        ts = []
+        for r in range(reps):
+            t0 = time.perf_counter()
+            adj, qs, _ = sampling.sample_layers(A, verts, fanouts, plan, mode=mode, seed=r + 1)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        edges = sum(a.nnz for a in adj)
+        out[name] = {"ms": 1e3 * statistics.median(ts), "sampled_edges": int(edges),
+                     "frontier_sizes": [q.rows for q in qs],
+                     "edges_per_s": edges / statistics.median(ts)}
+    return out
+
+
 def pattern_served(n_requests: int, device, A_big=None, S_big=None, St_big=None):
     """Mixed requests (R-MAT / ER A*B with n log-uniform in [1e3, 1e6] and
     degree U[4, 32], an MCL expansion M*M, graph contraction S^T A) arriving
@@ -636,6 +668,8 @@ def run_ours(args):
         patterns["batched_gnn"] = pattern_batched(args.gnn_graphs, dev)
         torch.cuda.empty_cache()
         patterns["mcl"] = pattern_mcl(dev)
+        torch.cuda.empty_cache()
+        patterns["bulk_sampling"] = pattern_sampling(A, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -283,6 +283,40 @@ int spgemm_csr_scatter_dense(const spgemm_plan* plan, const spgemm_csr* M, const
 int spgemm_csr_gather_dense(const spgemm_plan* plan, const spgemm_csr* M, const float* D,
                             int64_t ldd, float* out, void* ws, size_t ws_bytes, void* stream);
 
+/* --- Matrix-based bulk neighbourhood sampling (Section IV-C, mini-batch
+ * training): per layer P = Q^l * A (spgemm), NORM, Q^{l-1} = SAMPLE(P, s)
+ * and EXTRACT(A, Q^l, Q^{l-1}) = (Q^l * A) * S with S the selector of
+ * Q^{l-1}'s vertices. */
+
+/* SAMPLE: for each row of P draw s entries (1 <= s <= 32) by inverse
+ * transform sampling with the caller's uniforms u [P->rows * s] in [0, 1)
+ * (row-major, device): mode 0 uniform over the row's entries (entry
+ * floor(u * len)); mode 1 proportional to the values (negative values count
+ * as 0); mode 2 proportional to the squared values; modes 1-2 use fp64
+ * cumulative weights and take the first entry whose prefix exceeds
+ * u * total (a row of zero weight samples uniformly). A row with at most s
+ * entries keeps them all. Repeated draws collapse: Q's row holds the
+ * distinct drawn columns in ascending order, each with value 1 (at most s).
+ * Outputs (device): row_ptr_Q [P->rows+1], col_Q / val_Q [P->rows * s].
+ * nnz_Q [host, nullable]: non-NULL synchronises. Workspace:
+ * spgemm_workspace_bytes for a matrix of P->rows rows. Errors:
+ * SPGEMM_ERR_UNSUPPORTED for s outside 1..32. */
+int spgemm_sample_rows(const spgemm_plan* plan, const spgemm_csr* P, int32_t s, const float* u,
+                       int32_t mode, void* ws, size_t ws_bytes, int32_t* row_ptr_Q,
+                       int32_t* col_Q, float* val_Q, int64_t* nnz_Q, void* stream);
+
+/* The distinct columns of Q (the vertices Q^{l-1} selected), as
+ *   S (Q->cols x m): S[v, r] = 1 for the r-th selected vertex v (ascending),
+ *     row_ptr S_row_ptr [Q->cols+1] (also the rank of every vertex);
+ *   F (m x Q->cols): its transpose, one row per selected vertex (the next
+ *     layer's Q), row_ptr F_row_ptr [m+1];
+ * S_col/S_val/F_col/F_val hold at least min(Q->cols, Q->nnz) entries
+ * (device). m [host, nullable]: non-NULL synchronises. Workspace:
+ * spgemm_workspace_bytes for a matrix of Q->cols rows. */
+int spgemm_select_columns(const spgemm_plan* plan, const spgemm_csr* Q, void* ws, size_t ws_bytes,
+                          int32_t* S_row_ptr, int32_t* S_col, float* S_val, int32_t* F_row_ptr,
+                          int32_t* F_col, float* F_val, int64_t* m, void* stream);
+
 /* Synchronise `stream`, read and clear the workspace's device status word;
  * *status receives the SPGEMM_ERR_* code it maps to (SPGEMM_OK if clean). */
 int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status);

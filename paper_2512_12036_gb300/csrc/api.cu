@@ -573,6 +573,46 @@ int spgemm_csr_gather_dense(const spgemm_plan* plan, const spgemm_csr* M, const 
     return cuda_err(cudaGetLastError());
 }
 
+int spgemm_sample_rows(const spgemm_plan* plan, const spgemm_csr* P, int32_t s, const float* u,
+                       int32_t mode, void* ws, size_t ws_bytes, int32_t* row_ptr_Q,
+                       int32_t* col_Q, float* val_Q, int64_t* nnz_Q, void* stream) {
+    if (!plan) return SPGEMM_ERR_INVALID;
+    int rc = check_csr(P, mode != 0);
+    if (rc) return rc;
+    if (s < 1 || s > 32) return SPGEMM_ERR_UNSUPPORTED;
+    if (mode < 0 || mode > 2 || !row_ptr_Q) return SPGEMM_ERR_INVALID;
+    if (P->rows > 0 && (!u || !col_Q || !val_Q)) return SPGEMM_ERR_INVALID;
+    WsLayout L = ws_layout(plan, P->rows, 0, 0);
+    if (!ws || ws_bytes < L.total || ((uintptr_t)ws & 255)) return SPGEMM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    launch_sample_rows(plan, dev_view(P), s, u, mode, w, row_ptr_Q, col_Q, val_Q, st);
+    rc = cuda_err(cudaGetLastError());
+    if (rc) return rc;
+    if (nnz_Q) return sync_read(w.ctl, 2, nnz_Q, st);
+    return SPGEMM_OK;
+}
+
+int spgemm_select_columns(const spgemm_plan* plan, const spgemm_csr* Q, void* ws, size_t ws_bytes,
+                          int32_t* S_row_ptr, int32_t* S_col, float* S_val, int32_t* F_row_ptr,
+                          int32_t* F_col, float* F_val, int64_t* m, void* stream) {
+    if (!plan) return SPGEMM_ERR_INVALID;
+    int rc = check_csr(Q, false);
+    if (rc) return rc;
+    if (!S_row_ptr || !F_row_ptr) return SPGEMM_ERR_INVALID;
+    if (Q->cols > 0 && (!S_col || !S_val || !F_col || !F_val)) return SPGEMM_ERR_INVALID;
+    WsLayout L = ws_layout(plan, Q->cols, 0, 0);
+    if (!ws || ws_bytes < L.total || ((uintptr_t)ws & 255)) return SPGEMM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(L, ws, plan->opts.panel_cols);
+    launch_select_columns(plan, dev_view(Q), w, S_row_ptr, S_col, S_val, F_row_ptr, F_col, F_val,
+                          st);
+    rc = cuda_err(cudaGetLastError());
+    if (rc) return rc;
+    if (m) return sync_read(w.ctl, 2, m, st);
+    return SPGEMM_OK;
+}
+
 int spgemm_status(const spgemm_plan* plan, void* ws, void* stream, int* status) {
     if (!plan || !ws || !status) return SPGEMM_ERR_INVALID;
     *status = sync_read((Ctl*)ws, -1, nullptr, (cudaStream_t)stream);

@@ -153,6 +153,13 @@ void launch_backward(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
                      const int* colC, const float* dC, float* dA, float* dB, const WsPtrs& w,
                      double* dB64, double* dA64, cudaStream_t s);
 size_t backward_extra_bytes(long long a_nnz, long long b_nnz);
+__global__ void k_fill_i32(int* p, long long n, int v);
+void launch_sample_rows(const spgemm_plan* p, const CsrDev& P, int s, const float* u, int mode,
+                        const WsPtrs& w, int* rpt_out, int* col_out, float* val_out,
+                        cudaStream_t st);
+void launch_select_columns(const spgemm_plan* p, const CsrDev& Q, const WsPtrs& w, int* S_rpt,
+                           int* S_col, float* S_val, int* F_rpt, int* F_col, float* F_val,
+                           cudaStream_t st);
 void launch_topk(const spgemm_plan* p, const float* X, int n, int d, long long ldx, int k,
                  int* rpt, int* col, float* val, cudaStream_t s);
 void launch_scatter_dense(const spgemm_plan* p, const CsrDev& M, const float* vals, float* X,
