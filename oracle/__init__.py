@@ -5,9 +5,11 @@ CPU-baseline leg are the only callers. The library path never imports this
 package, and this package imports nothing from the library; the two share
 only the seeded input generators.
 
-The arithmetic lives in ``oracle.c`` (plain C, fp64, optional OpenMP over
-rows); this module builds it with gcc on first use and marshals numpy arrays.
-Which passage of the paper each function restates is given in ``oracle.c``.
+The SpGEMM arithmetic lives in ``oracle.c`` (plain C, fp64, optional OpenMP
+over rows); this module builds it with gcc on first use and marshals numpy
+arrays. Which passage of the paper each function restates is given in
+``oracle.c``. The pruned GNN layer (``layers.py``) and bulk sampling
+(``sampling.py``) are plain numpy in fp64 on small inputs.
 """
 from __future__ import annotations
 
