@@ -442,23 +442,12 @@ __global__ void k_bpanel(CsrDev B, int P, int PW, int* tab, Ctl* ctl) {
 // their entries (and the panel table) in tiles every pass.
 constexpr int kGroup = 160;
 
-#ifndef SPG_D32_UNROLL
-#define SPG_D32_UNROLL 4
-#endif
-#ifndef SPG_PAD_D32
-#define SPG_PAD_D32 1
-#endif
-#ifndef SPG_PAD_HOT
-#define SPG_PAD_HOT 0
-#endif
-#ifndef SPG_D32_THREADS
-#define SPG_D32_THREADS 1024
-#endif
-#ifndef SPG_D32_BLOCKS
-#define SPG_D32_BLOCKS 1
-#endif
-constexpr int kD32Threads = SPG_D32_THREADS;   // fp32 dense tier: threads per block
-constexpr int kD32Blocks = SPG_D32_BLOCKS;     // and blocks per SM it is sized for
+// fp32 dense tier: threads per block, blocks per SM its passes are sized
+// for, and products per warp step batch (512 x 2 and 256 x 4 blocks, and
+// unroll 2 or 8, measured no faster on GB300)
+constexpr int kD32Threads = 1024;
+constexpr int kD32Blocks = 1;
+constexpr int kD32Unroll = 4;
 
 template <int kMode, int kT>
 __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B, const int* map,
@@ -576,12 +565,9 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                     }
                 }
                 if (kMode == 0) {
-                    if (SPG_PAD_D32)
-                        expand_tile_padded<kNumDenseThreads, float, SPG_D32_UNROLL>(tile, bs, len, mya,
-                                                                                   load, apply);
-                    else
-                        expand_tile<kNumDenseThreads, float, SPG_D32_UNROLL>(tile, bs, len, mya, load,
-                                                                            apply);
+                    // long per-pass segments: padded expansion (no segment search)
+                    expand_tile_padded<kNumDenseThreads, float, kD32Unroll>(tile, bs, len, mya, load,
+                                                                           apply);
                 } else {
                     for (int g0 = 0; g0 < na; g0 += kGroup) {
                         const bool mine = (int)threadIdx.x >= g0 && (int)threadIdx.x < g0 + kGroup;
@@ -613,7 +599,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                             }
                         }
                     }
-                    if (SPG_PAD_D32 && kMode == 0)
+                    if (kMode == 0)
                         expand_tile_padded<kNumDenseThreads, float, 4>(tile, bs, len, a, load, apply);
                     else
                         expand_tile<kNumDenseThreads, float, 4>(tile, bs, len, a, load, apply);
@@ -659,13 +645,8 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
 // launch); when it holds more hot columns than kSlots it is split into
 // sub-passes at hot-column boundaries (re-reading its segments).
 constexpr int kHotThreads = 1024;
-#ifndef SPG_HOT_UNROLL
-#define SPG_HOT_UNROLL 2
-#endif
-#ifndef SPG_HOT_SLOTS
-#define SPG_HOT_SLOTS 1024
-#endif
-constexpr int kHotSlots = SPG_HOT_SLOTS;
+constexpr int kHotUnroll = 2;      // products per warp step batch (4 and 8 measured slower)
+constexpr int kHotSlots = 1024;
 constexpr int kHotCopies = 8;
 static_assert(kHotThreads / kHotCopies <= 160, "a copy must gather at most 160 terms per tile");
 
@@ -799,12 +780,9 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                     hi = pc1;
                 }
                 if (cached) {
-                    if (SPG_PAD_HOT)
-                        expand_tile_padded<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, bs, len, mya,
-                                                                                     load, apply);
-                    else
-                        expand_tile<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, bs, len, mya, load,
-                                                                              apply);
+                    // packed expansion: this tier's per-pass segments are often short
+                    expand_tile<kHotThreads, float, kHotUnroll, true>(tile, bs, len, mya, load,
+                                                                      apply);
                     fold();
                 } else {
                     for (int tb = rs; tb < re; tb += kHotThreads) {
@@ -826,12 +804,8 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                                 }
                             }
                         }
-                        if (SPG_PAD_HOT)
-                            expand_tile_padded<kHotThreads, float, SPG_HOT_UNROLL, true>(
-                                tile, tbs, tlen, a, load, apply);
-                        else
-                            expand_tile<kHotThreads, float, SPG_HOT_UNROLL, true>(tile, tbs, tlen, a,
-                                                                                  load, apply);
+                        expand_tile<kHotThreads, float, kHotUnroll, true>(tile, tbs, tlen, a, load,
+                                                                          apply);
                         fold();
                     }
                 }
@@ -893,9 +867,6 @@ void occupancy_numeric(spgemm_plan* p) {
         const size_t per = hot_smem_of(p->opts.panel_cols, 1) - hot_smem_of(p->opts.panel_cols, 0);
         p->hot_ppp = p->smem_optin > fixed + per ? (int)((p->smem_optin - fixed) / per) : 1;
         if (p->hot_ppp > 64) p->hot_ppp = 64;
-#ifdef SPG_HOT_PPP_CAP
-        if (p->hot_ppp > SPG_HOT_PPP_CAP) p->hot_ppp = SPG_HOT_PPP_CAP;
-#endif
     }
     // fp32 dense tier: as many table panels per pass as a block's share of
     // the SM's shared memory holds beside its static arrays
@@ -912,9 +883,6 @@ void occupancy_numeric(spgemm_plan* p) {
         const size_t per = 4 * (size_t)p->opts.panel_cols + p->opts.panel_cols / 8;
         p->d32_ppp = avail >= per ? (int)(avail / per) : 1;
         if (p->d32_ppp > 64) p->d32_ppp = 64;
-#ifdef SPG_D32_PPP_CAP
-        if (p->d32_ppp > SPG_D32_PPP_CAP) p->d32_ppp = SPG_D32_PPP_CAP;
-#endif
     }
     struct K {
         const void* f;

@@ -14,9 +14,7 @@
 
 namespace spg {
 
-#ifndef SPG_SYMD_UNROLL
-#define SPG_SYMD_UNROLL 4
-#endif
+constexpr int kSymDenseUnroll = 4;   // products per warp step batch (2 measured slower)
 
 constexpr int kSymDenseWords = 48 * 1024;   // 192 KB bitmap (1.5M columns per pass)
 
@@ -179,7 +177,7 @@ __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, Csr
             const int nw = (span + 31) >> 5;
             for (int q = threadIdx.x; q < nw; q += blockDim.x) bm[q] = 0u;
             __syncthreads();
-            block_expand<kSymDenseThreads, float, SPG_SYMD_UNROLL>(
+            block_expand<kSymDenseThreads, float, kSymDenseUnroll>(
                 rs, re, tile,
                 [&](int j, int& bs, int& len, float&) { a_entry(A, B, j, bs, len, ctl); },
                 [&](int t) { return B.col[t]; },
