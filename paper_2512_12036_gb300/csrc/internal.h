@@ -40,6 +40,8 @@ struct spgemm_plan {
     int occ_num_dense32, occ_num_dense64, occ_num_dense_hot;
     int hot_ppp;           // table panels per pass of the fp64 dense tier
     int d32_ppp;           // and of the fp32 dense tier
+    size_t rank_budget;    // dynamic shared memory of the rank-compacted fp32 dense kernel
+    int occ_num_rank;
 };
 
 namespace spg {

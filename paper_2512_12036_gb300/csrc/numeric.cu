@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                                                             int row_begin, int* colC,
                                                             float* valC, int bin_lo, int bin_hi,
                                                             int tier, const int* tab, int P,
-                                                            int PW, int ppp) {
+                                                            int PW, int ppp, int only_uncached) {
     constexpr int kNumDenseThreads = kT;
     const int kPanelsPerPass = kMode == 0 ? ppp : 1;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -530,6 +530,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
         row_extent(A, row, rs, re, ctl);
         const int na = re - rs;
         const bool cached = use_tab && na <= kNumDenseThreads;
+        if (only_uncached && cached) continue;       // the rank-compacted kernel's row
         int myk = -1, cur = 0, nxt = 0;
         float mya = 0.f;
         if (cached && (int)threadIdx.x < na) {
@@ -622,6 +623,181 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                 });
         }
         if (threadIdx.x == 0 && written != nnz_row) set_status(ctl, ST_INTERNAL);
+    }
+}
+
+// fp32 dense tier with rank-compacted passes (rows whose A entries fit the
+// block and whose B rows are sorted; k_num_dense<0> takes the others). A
+// pass covers up to kRankPanels table panels; the row's occupancy is
+// recorded first (a bitmap expansion: one atomicOr per product), then each
+// bitmap word gets the rank of its first entry among the pass's entries and
+// the pass's columns are written out, then a second expansion adds every
+// product into a compact value array at its entry's rank (word rank + the
+// popcount of the lower bits), which is streamed out with coalesced stores.
+// Shared memory per column is a bit and a 1/32 rank instead of a 4-byte
+// value, so a pass spans many more columns than a dense value array allows:
+// the passes per row, whose fixed cost (block scans, barriers, short
+// per-warp work) dominates that tier, drop. The panels per pass are chosen
+// per row so that the expected entries of a pass (nnz_row / P per panel)
+// stay within 3/4 of the value array; a pass that still holds more is
+// accumulated in word ranges of at most `cap` entries.
+constexpr int kRankPanels = 16;
+
+__global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, CsrDev B,
+                                                                   const int* map, Ctl* ctl,
+                                                                   const int* rptC, int row_begin,
+                                                                   int* colC, float* valC,
+                                                                   int bin_lo, int bin_hi, int tier,
+                                                                   const int* tab, int P, int PW,
+                                                                   int pmax, int cap) {
+    constexpr int kT = kD32Threads;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int RW = (pmax * PW) >> 5;                  // words of the widest pass
+    unsigned* bm = reinterpret_cast<unsigned*>(sm_raw);
+    int* rk = reinterpret_cast<int*>(bm + RW);
+    float* vals = reinterpret_cast<float*>(rk + RW);
+    __shared__ int s_idx, s_hi;
+    __shared__ int scratch[33];
+    __shared__ ExpandTile<kT, float> tile;
+    const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
+    if (begin >= end) return;
+    if (tab == nullptr || (ctl->b_unsorted & 1) != 0) return;     // fallback kernel's rows
+    const int t = threadIdx.x;
+    for (int i = t; i < RW; i += kT) bm[i] = 0u;
+    for (int i = t; i < cap; i += kT) vals[i] = 0.f;
+    const long long stride = P + 1;
+
+    int c0 = 0, span = 0, lo = 0, hi = 0, rbase = 0;
+    auto load_key = [&](int q) { return B.col[q]; };
+    auto mark = [&](int key, float) {
+        if (!key_in(key, B, ctl)) return;
+        const int kk = key - c0;
+        if ((unsigned)kk < (unsigned)span) atomicOr(&bm[kk >> 5], 1u << (kk & 31));
+        else set_status(ctl, ST_INTERNAL);
+    };
+    auto load = [&](int q) { return KeyVal{B.col[q], B.val[q]}; };
+    auto add = [&](KeyVal kv, float a) {
+        if (!key_in(kv.key, B, ctl)) return;
+        const int kk = kv.key - c0;
+        const int w = kk >> 5;
+        if ((unsigned)kk >= (unsigned)span || w < lo || w >= hi) return;   // other word range
+        const int r = rk[w] + __popc(bm[w] & ((1u << (kk & 31)) - 1u)) - rbase;
+        if ((unsigned)r < (unsigned)cap) atomicAdd(&vals[r], a * kv.v);
+        else set_status(ctl, ST_INTERNAL);
+    };
+
+    for (;;) {
+        if (t == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= end) break;
+        const int r = map[idx];
+        const int row = row_begin + r;
+        const int out = rptC[r];
+        const int nnz_row = rptC[r + 1] - out;
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        const int na = re - rs;
+        if (na > kT) continue;                        // fallback kernel's row
+        const long long per_panel = ((long long)nnz_row + P - 1) / P;
+        long long want = per_panel > 0 ? (3ll * cap / 4) / per_panel : pmax;
+        const int ppp = (int)(want < 1 ? 1 : (want > pmax ? pmax : want));
+        const int npass = (P + ppp - 1) / ppp;
+        int myk = -1, cur = 0, nxt = 0;
+        float mya = 0.f;
+        if (t < na) {
+            const int j = rs + t;
+            const int k = A.col[j];
+            if ((unsigned)k < (unsigned)B.rows) {
+                myk = k;
+                mya = A.val[j];
+                cur = tab[(long long)k * stride];
+                nxt = tab[(long long)k * stride + (ppp < P ? ppp : P)];
+            } else {
+                set_status(ctl, ST_INVALID);
+            }
+        }
+        int written = 0;
+        for (int pass = 0; pass < npass; ++pass) {
+            const int p0 = pass * ppp;
+            const int p1 = p0 + ppp < P ? p0 + ppp : P;
+            c0 = p0 * PW;
+            span = (int)(B.cols - (long long)c0 < (long long)(p1 - p0) * PW ? B.cols - (long long)c0
+                                                                            : (long long)(p1 - p0) * PW);
+            int nxt2 = 0;
+            if (myk >= 0 && pass + 1 < npass)
+                nxt2 = tab[(long long)myk * stride + (p1 + ppp < P ? p1 + ppp : P)];
+            int bs = 0, len = 0;
+            if (myk >= 0) {
+                if (cur < 0 || nxt < cur || (long long)nxt > B.nnz) set_status(ctl, ST_INTERNAL);
+                else {
+                    bs = cur;
+                    len = nxt - cur;
+                }
+            }
+            // 1. occupancy
+            expand_tile_padded<kT, float, kD32Unroll>(tile, bs, len, mya, load_key, mark);
+            // 2. word ranks and the pass's columns (thread t owns words [wb, wb + wpt))
+            const int nw = (span + 31) >> 5;
+            const int wpt = (nw + kT - 1) / kT;
+            const int wb = t * wpt;
+            int cnt = 0;
+            for (int q = 0; q < wpt; ++q)
+                if (wb + q < nw) cnt += __popc(bm[wb + q]);
+            int tot;
+            int run = block_excl_scan(cnt, scratch, &tot);
+            for (int q = 0; q < wpt; ++q) {
+                const int w = wb + q;
+                if (w >= nw) break;
+                rk[w] = run;
+                unsigned bits = bm[w];
+                while (bits) {
+                    const int o = written + run;
+                    if (o < nnz_row) colC[out + o] = c0 + w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    ++run;
+                }
+            }
+            __syncthreads();
+            // 3. values, in word ranges of at most cap entries
+            for (lo = 0; lo < nw; lo = hi) {
+                if (t == 0) {
+                    const int base_lo = rk[lo];
+                    int h;
+                    if (tot - base_lo <= cap) {
+                        h = nw;
+                    } else {                          // largest h with rank(h) - rank(lo) <= cap
+                        int a = lo + 1, b = nw - 1;
+                        while (a < b) {
+                            const int mid = (a + b + 1) >> 1;
+                            if (rk[mid] - base_lo <= cap) a = mid;
+                            else b = mid - 1;
+                        }
+                        h = a;
+                    }
+                    s_hi = h;
+                }
+                __syncthreads();
+                hi = s_hi;
+                rbase = rk[lo];
+                const int cnt_sub = (hi < nw ? rk[hi] : tot) - rbase;
+                expand_tile_padded<kT, float, kD32Unroll>(tile, bs, len, mya, load, add);
+                for (int i = t; i < cnt_sub; i += kT) {
+                    const int o = written + rbase + i;
+                    if (o < nnz_row) valC[out + o] = vals[i];
+                    vals[i] = 0.f;
+                }
+                __syncthreads();
+            }
+            for (int q = 0; q < wpt; ++q)
+                if (wb + q < nw) bm[wb + q] = 0u;
+            written += tot;
+            __syncthreads();
+            cur = nxt;
+            nxt = nxt2;
+        }
+        if (t == 0 && written != nnz_row) set_status(ctl, ST_INTERNAL);
     }
 }
 
@@ -845,6 +1021,18 @@ static size_t num_warp_smem(size_t acc) { return (acc + 4) * kWarpsPerBlockNW * 
 static size_t num_block_smem(const spgemm_plan* p, size_t acc) {
     return (acc + 4) * pow2_ceil(2u * (unsigned)p->opts.block_max_nnz);
 }
+// rank-compacted fp32 dense kernel: bitmap + word ranks of pmax panels,
+// then as many fp32 values as the rest holds (at most 32768, leaving L1
+// some room)
+static int rank_cap(const spgemm_plan* p, int pmax, int pw) {
+    const size_t words = (size_t)pmax * pw / 32 * 8;
+    const size_t left = p->rank_budget > words ? (p->rank_budget - words) / 4 : 0;
+    return (int)(left > 32768 ? 32768 : left);
+}
+static size_t rank_smem(const spgemm_plan* p, int pmax, int pw) {
+    return (size_t)pmax * pw / 32 * 8 + 4 * (size_t)rank_cap(p, pmax, pw);
+}
+
 static size_t num_dense_hot_smem(const spgemm_plan* p) {
     return hot_smem_of(p->opts.panel_cols, p->hot_ppp);
 }
@@ -884,12 +1072,19 @@ void occupancy_numeric(spgemm_plan* p) {
         p->d32_ppp = avail >= per ? (int)(avail / per) : 1;
         if (p->d32_ppp > 64) p->d32_ppp = 64;
     }
+    {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, (const void*)k_num_dense_rank);
+        p->rank_budget = p->smem_optin > fa.sharedSizeBytes ? p->smem_optin - fa.sharedSizeBytes : 0;
+    }
     struct K {
         const void* f;
         int threads;
         size_t smem;
         int* occ;
     } ks[] = {
+        {(const void*)k_num_dense_rank, kD32Threads, rank_smem(p, kRankPanels, p->opts.panel_cols),
+         &p->occ_num_rank},
         {(const void*)k_num_warp<float>, kWarpsPerBlockNW * 32, num_warp_smem(4), &p->occ_num_warp32},
         {(const void*)k_num_warp<double>, kWarpsPerBlockNW * 32, num_warp_smem(8), &p->occ_num_warp64},
         {(const void*)k_num_block<float>, kNumBlockThreads, num_block_smem(p, 4), &p->occ_num_block32},
@@ -966,10 +1161,25 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                k_num_block<double><<<sms * p->occ_num_block64, kNumBlockThreads, num_block_smem(p, 8), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits));
     const int PW = w.panel_cols;
-    SPG_LAUNCH(p, K_NUM_DENSE32, s,
-               k_num_dense<0, kD32Threads><<<sms * p->occ_num_dense32, kD32Threads, num_dense_smem(p, 0), s>>>(
-                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
-                   NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW, p->d32_ppp));
+    const int pmax = w.panels < kRankPanels ? w.panels : kRankPanels;
+    const int cap = w.bpanel ? rank_cap(p, pmax, PW) : 0;
+    if (w.bpanel && cap >= 1024) {
+        // rank-compacted passes for the rows it takes, then the dense-array
+        // kernel for the rest (B unsorted, or more A entries than threads)
+        SPG_LAUNCH(p, K_NUM_DENSE32, s,
+                   k_num_dense_rank<<<sms * p->occ_num_rank, kD32Threads, rank_smem(p, pmax, PW), s>>>(
+                       A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
+                       NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW, pmax, cap));
+        SPG_LAUNCH(p, K_NUM_DENSE32, s,
+                   k_num_dense<0, kD32Threads><<<sms * p->occ_num_dense32, kD32Threads, num_dense_smem(p, 0), s>>>(
+                       A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
+                       NB_DENSE32_0 + NB_DENSE_N, 6, w.bpanel, w.panels, PW, p->d32_ppp, 1));
+    } else {
+        SPG_LAUNCH(p, K_NUM_DENSE32, s,
+                   k_num_dense<0, kD32Threads><<<sms * p->occ_num_dense32, kD32Threads, num_dense_smem(p, 0), s>>>(
+                       A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
+                       NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW, p->d32_ppp, 0));
+    }
     if (w.bhot && w.bpanel) {
         SPG_LAUNCH(p, K_NUM_DENSE64, s,
                    k_num_dense_hot<<<sms * p->occ_num_dense_hot, kHotThreads, num_dense_hot_smem(p), s>>>(
@@ -981,7 +1191,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     SPG_LAUNCH(p, K_NUM_DENSE64, s,
                k_num_dense<1, 1024><<<sms * p->occ_num_dense64, 1024, num_dense_smem(p, 1), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
-                   NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW, 1));
+                   NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW, 1, 0));
 }
 
 }  // namespace spg

@@ -231,6 +231,29 @@ def test_plans_with_different_tables_interleave(plan):
     check_product(plan, A, B)
 
 
+def test_dense_tier_clustered_pass_overflow(plan):
+    # a row of the fp32 dense tier (160 A entries) whose ~42k output columns
+    # all sit in the first of 20 panels: sized for an even spread, its first
+    # pass holds more entries than the compact value array and is
+    # accumulated in word ranges
+    rng = np.random.default_rng(81)
+    cols, nb = 20 * 16384, 200
+    r, c = [], []
+    for k in range(nb):
+        cc = rng.choice(50000, size=600, replace=False) if k < 160 else \
+            rng.choice(cols, size=50, replace=False)
+        r.append(np.full(cc.size, k))
+        c.append(cc)
+    r, c = np.concatenate(r), np.concatenate(c)
+    B = gen.csr_from_coo(nb, cols, r, c, gen.uniform_open_closed(rng, r.size))
+    A = gen.csr_from_coo(3, nb, np.concatenate([np.zeros(160), np.ones(40), np.full(30, 2)]),
+                         np.concatenate([np.arange(160), np.arange(160, 200), np.arange(0, 30)]),
+                         np.ones(230, np.float32))
+    nnz = oracle.symbolic(A, B)
+    assert nnz[0] > 40000 and np.diff(A.row_ptr)[0] <= 167
+    check_product(plan, A, B)
+
+
 def test_dense_tier_unsorted_b(plan):
     B = hub_matrix(500, 50000, 7, heavy_rows=set(range(0, 500, 3)), heavy_len=400)
     Bu = gen.random_csr(1, 1, 1.0, 0)  # placeholder for type
