@@ -139,7 +139,7 @@ class ClockSampler:
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
 
     def summary(self):
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, power = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in getattr(self, "lines", []):
             f = [x.strip() for x in ln.split(",")]
@@ -150,13 +150,18 @@ class ClockSampler:
                 smax = float(f[2])
             except ValueError:
                 continue
+            try:
+                power.append(float(f[3].split()[0]))
+            except (ValueError, IndexError):
+                pass
             for n, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "sm_mhz_min": min(sm),
+                "power_w": statistics.median(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ---------------------------------------------------------------------------
@@ -646,15 +651,17 @@ def run_ours(args):
         e2e_step()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        e1.record(stream)
-        barrier()
+        with ClockSampler(local) as clk_e2e:
+            e0.record(stream)
+            for _ in range(args.steps):
+                e2e_step()
+            e1.record(stream)
+            barrier()
         ems = e0.elapsed_time(e1)
         ems = max_over_ranks(ems, dev)
         e2e = {"value": 2.0 * ip_step * world / (ems / args.steps / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "clocks": clk_e2e.summary(),
                "note": "inputs copied from pinned host memory each step; C(S^T A S) and the "
                        "row pointers of every A*A block read back (the A*A values stay in HBM)"}
 
