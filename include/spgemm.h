@@ -185,7 +185,9 @@ int spgemm_numeric(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_cs
  *   product of row i reaches (otherwise SPGEMM_ERR_INVALID on the status).
  * dC [device, nnz_C]: the gradient on C's stored values.
  * dA [out, device, A.nnz, nullable], dB [out, device, B.nnz, nullable]:
- *   fully overwritten; sums are accumulated in fp64 and rounded once.
+ *   fully overwritten (an entry that meets no product, e.g. an A entry
+ *   whose row of B is empty, gets 0); sums are accumulated in fp64 and
+ *   rounded once.
  * Workspace: spgemm_backward_workspace_bytes (includes B.nnz + A.nnz fp64
  * slots). Does not synchronise. C must fit int32 row pointers. */
 int spgemm_backward_workspace_bytes(const spgemm_plan* plan, const spgemm_csr* A,

@@ -321,6 +321,9 @@ void launch_backward(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
               w.panel_cols};
     if (dB && B.nnz > 0)
         SPG_LAUNCH(p, K_BWD, s, k_bwd_zero<<<sms * 4, 256, 0, s>>>(dB64, B.nnz));
+    // rows whose C row is empty are never visited: their A entries have no
+    // product, so their gradient is 0
+    if (dA && A.nnz > 0) cudaMemsetAsync(dA, 0, sizeof(float) * (size_t)A.nnz, s);
     // the heavy tier needs B's panel table (built into this workspace)
     launch_bpanel(p, B, w, s);
     x.tab = w.bpanel;

@@ -1,4 +1,5 @@
-"""Seeded random products against the oracle under random plan options.
+"""Seeded random products and their backward against the oracle under random
+plan options.
 
 Small panels (1024 columns), low block-tier limits and low hash-tier limits
 push small matrices through the multi-pass, multi-panel and word-range
@@ -70,3 +71,10 @@ def test_random_product(seed):
     C = plan.spgemm(DeviceCSR.from_host(A), DeviceCSR.from_host(B))
     torch.cuda.synchronize()
     compare(C.to_host(), oracle.spgemm(A, B))
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_backward(seed):
+    from test_gpu_backward import check_backward
+    A, B = random_problem(1000 + seed)
+    check_backward(Plan(**OPTION_SETS[seed % len(OPTION_SETS)]), A, B, seed=seed)
