@@ -14,7 +14,8 @@ enum KernelId : int {
     K_FILL, K_CHECK_RPT, K_ZERO, K_IP_COUNT, K_SUM, K_GROUP_HIST, K_GROUP_SCAN, K_GROUP_SCATTER,
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_FINAL, K_RESET, K_BPANEL, K_SYM_ESC, K_SYM_WARP, K_SYM_BLOCK,
     K_SYM_DENSE, K_NUM_ESC, K_NUM_WARP32, K_NUM_WARP64, K_NUM_BLOCK32, K_NUM_BLOCK64,
-    K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_GUARD, K_MCL, K_HOT, K_LAYER, K_NUM_KERNELS
+    K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_GUARD, K_MCL, K_HOT, K_LAYER, K_SYM_NARROW,
+    K_NUM_NARROW, K_NUM_KERNELS
 };
 extern const char* const kKernelNames[K_NUM_KERNELS];
 
@@ -68,8 +69,15 @@ constexpr int kMaxPanels = 1024;    // above this the heavy path filters whole B
 enum : int {
     SB_ESC = 0, SB_WARP = 1, SB_BLOCK0 = 2, SB_BLOCK_N = 4, SB_DENSE0 = 6, SB_DENSE_N = 32,
     NB_ESC = 0, NB_WARP32 = 1, NB_WARP64 = 2, NB_BLOCK32 = 3, NB_BLOCK64 = 4,
-    NB_DENSE32_0 = 5, NB_DENSE_N = 16, NB_DENSE64_0 = 21
+    NB_DENSE32_0 = 5, NB_DENSE_N = 16, NB_DENSE64_0 = 21,
+    SB_NARROW = 38, NB_NARROW32 = 37, NB_NARROW64 = 38
 };
+
+// Narrow tiers: when B has at most kNarrowCols columns, rows with at most
+// kNarrowMaxIP products take one warp each with a dense per-warp
+// accumulator over all of B's columns (no hashing, no sort).
+constexpr int kNarrowCols = 1024;
+constexpr long long kNarrowMaxIP = 32768;
 
 // Backward tiers (grouping phase 3, by nnz of the row of C): dense lookup
 // when B has few columns, warp hash, block hash, dense column panels.
@@ -128,7 +136,7 @@ struct GroupArgs {
     const long long* key;      // generic: keys (n)
     const long long* thr;      // generic: thresholds
     int nthr;
-    int bcols;                 // backward: columns of B
+    int bcols;                 // columns of B (narrow tiers, backward dense tier)
     spgemm_opts opts;
 };
 void launch_group(const spgemm_plan* p, const GroupArgs& g, const WsPtrs& w, int* map_out,

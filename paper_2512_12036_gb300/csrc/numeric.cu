@@ -294,6 +294,67 @@ __global__ void __launch_bounds__(kWarpsPerBlockNW * 32) k_num_warp(CsrDev A, Cs
     }
 }
 
+// Narrow B (<= kNarrowCols columns): one warp per row accumulates into a
+// per-warp dense array over all of B's columns (fp32, or fp64 for rows
+// where more than fp32_max_terms products can meet) and marks the columns in
+// a 32-word bitmap; lane l owns word l, so a warp scan of the popcounts
+// writes the row in column order with no sort. Touched entries are cleared
+// on the way out, so the array stays zero between rows.
+constexpr int kNarrowWarps = 8;
+
+template <typename Acc>
+__global__ void __launch_bounds__(kNarrowWarps * 32) k_num_narrow(CsrDev A, CsrDev B,
+                                                                  const int* map, Ctl* ctl,
+                                                                  const int* rptC, int row_begin,
+                                                                  int* colC, float* valC, int bin,
+                                                                  int ncols_pad) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ unsigned bmw[kNarrowWarps][32];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    Acc* dense = reinterpret_cast<Acc*>(sm_raw) + warp * ncols_pad;
+    unsigned* bm = bmw[warp];
+    for (int c = lane; c < ncols_pad; c += 32) dense[c] = Acc(0);
+    bm[lane] = 0u;
+    __syncwarp();
+    const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int idx = begin + gw; idx < end; idx += nw) {
+        const int r = map[idx];
+        const int row = row_begin + r;
+        const int out = rptC[r];
+        const int nnz_row = rptC[r + 1] - out;
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        warp_expand(A, B, rs, re, 32, ctl, [&](int t, int ja) {
+            const int key = B.col[t];
+            if (key_in(key, B, ctl)) {
+                atomicOr(&bm[key >> 5], 1u << (key & 31));
+                atomicAdd(&dense[key], (Acc)A.val[ja] * (Acc)B.val[t]);
+            }
+        });
+        __syncwarp();
+        unsigned bits = bm[lane];
+        const int cnt = __popc(bits);
+        const int incl = warp_incl_scan(cnt);
+        int pos = incl - cnt;
+        const int tot = __shfl_sync(kFull, incl, 31);
+        while (bits) {
+            const int c = lane * 32 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (pos < nnz_row) {
+                colC[out + pos] = c;
+                valC[out + pos] = (float)dense[c];
+            }
+            dense[c] = Acc(0);
+            ++pos;
+        }
+        bm[lane] = 0u;
+        if (lane == 0 && tot != nnz_row) set_status(ctl, ST_INTERNAL);
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------------------
 template <typename Acc>
 __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev B,
@@ -1093,6 +1154,8 @@ void occupancy_numeric(spgemm_plan* p) {
         {(const void*)k_num_dense<1, 1024>, 1024, num_dense_smem(p, 1), &p->occ_num_dense64},
         {(const void*)k_num_dense_hot, kHotThreads, num_dense_hot_smem(p), &p->occ_num_dense_hot},
     };
+    allow_max_dynamic_smem((const void*)k_num_narrow<float>, p);
+    allow_max_dynamic_smem((const void*)k_num_narrow<double>, p);
     for (auto& k : ks) {
         allow_max_dynamic_smem(k.f, p);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(k.occ, k.f, k.threads, k.smem);
@@ -1138,6 +1201,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     g.ip = ip;
     g.rptA = A.rpt;
     g.rptC = rptC;
+    g.bcols = B.cols;
     g.opts = p->opts;
     launch_group(p, g, w, w.map, nullptr, s);
     if (g.n == 0) return;
@@ -1145,6 +1209,15 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
         SPG_LAUNCH(p, K_GUARD, s, k_cap_guard<<<1, 64, 0, s>>>(rptC, g.n, capacity, w.ctl));
     const int sms = p->num_sms;
     SPG_LAUNCH(p, K_NUM_ESC, s, k_num_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_ESC));
+    if (B.cols <= kNarrowCols) {
+        const int pad = (B.cols + 31) & ~31;
+        SPG_LAUNCH(p, K_NUM_NARROW, s,
+                   k_num_narrow<float><<<sms * 8, kNarrowWarps * 32, (size_t)kNarrowWarps * pad * 4, s>>>(
+                       A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_NARROW32, pad));
+        SPG_LAUNCH(p, K_NUM_NARROW, s,
+                   k_num_narrow<double><<<sms * 8, kNarrowWarps * 32, (size_t)kNarrowWarps * pad * 8, s>>>(
+                       A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_NARROW64, pad));
+    }
     SPG_LAUNCH(p, K_NUM_WARP32, s,
                k_num_warp<float><<<sms * p->occ_num_warp32, kWarpsPerBlockNW * 32, num_warp_smem(4), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP32));

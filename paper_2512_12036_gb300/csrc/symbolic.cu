@@ -195,6 +195,38 @@ __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, Csr
     }
 }
 
+// Narrow B (<= kNarrowCols columns): one warp per row marks the row's
+// columns in a per-warp bitmap of 32 words (word w holds columns 32w..32w+31)
+// and counts them; no table, no probing.
+constexpr int kNarrowWarps = 8;
+
+__global__ void __launch_bounds__(kNarrowWarps * 32) k_sym_narrow(CsrDev A, CsrDev B,
+                                                                  const int* map, Ctl* ctl,
+                                                                  int* row_nnz, int bin) {
+    __shared__ unsigned bmw[kNarrowWarps][32];
+    const int lane = lane_id();
+    unsigned* bm = bmw[threadIdx.x >> 5];
+    bm[lane] = 0u;
+    __syncwarp();
+    const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int idx = begin + gw; idx < end; idx += nw) {
+        const int row = map[idx];
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        warp_expand(A, B, rs, re, 32, ctl, [&](int t, int) {
+            const int key = B.col[t];
+            if (key_ok(key, B, ctl)) atomicOr(&bm[key >> 5], 1u << (key & 31));
+        });
+        __syncwarp();
+        const int cnt = warp_sum(__popc(bm[lane]));
+        bm[lane] = 0u;
+        __syncwarp();
+        if (lane == 0) row_nnz[row] = cnt;
+    }
+}
+
 // ---------------------------------------------------------------------------
 
 static size_t sym_dense_smem(const spgemm_plan* p) {
@@ -232,6 +264,7 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     g.ip = ip;
     g.rptA = A.rpt;
     g.row_nnz = row_nnz;
+    g.bcols = B.cols;
     g.opts = p->opts;
     launch_group(p, g, w, w.map, nullptr, s);
     if (A.rows == 0) return;
@@ -247,6 +280,10 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     SPG_LAUNCH(p, K_SYM_BLOCK, s,
                k_sym_block<<<sms * p->occ_sym_block, kSymBlockThreads, (size_t)tb * 4, s>>>(
                    A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, SB_BLOCK0 + SB_BLOCK_N, 0, max_bits));
+    if (B.cols <= kNarrowCols)
+        SPG_LAUNCH(p, K_SYM_NARROW, s,
+                   k_sym_narrow<<<sms * 8, kNarrowWarps * 32, 0, s>>>(A, B, w.map, w.ctl, row_nnz,
+                                                                     SB_NARROW));
     const size_t sd = sym_dense_smem(p);
     SPG_LAUNCH(p, K_SYM_DENSE, s,
                k_sym_dense<<<sms * p->occ_sym_dense, kSymDenseThreads, sd, s>>>(

@@ -254,6 +254,25 @@ def test_dense_tier_clustered_pass_overflow(plan):
     check_product(plan, A, B)
 
 
+def test_narrow_b_tiers(plan):
+    # B with 700 columns: rows in the in-register tier, the narrow fp32 and
+    # fp64 tiers (more than 167 A entries), and rows above the narrow tier's
+    # product limit (block and dense tiers)
+    rng = np.random.default_rng(91)
+    k, n = 3000, 700
+    B = gen.random_csr(k, n, 0.03, seed=92)                 # ~21 entries per row
+    r, c = [], []
+    for i, d in enumerate([3, 10, 60, 150, 170, 400, 900, 2500, 2999, 1, 0, 40]):
+        cc = rng.choice(k, size=d, replace=False)
+        r.append(np.full(d, i))
+        c.append(cc)
+    r, c = np.concatenate(r), np.concatenate(c)
+    A = gen.csr_from_coo(12, k, r, c, gen.uniform_open_closed(rng, r.size))
+    ip, _ = oracle.ip_count(A, B)
+    assert ip.max() > 32768 and (ip[(np.diff(A.row_ptr) > 167)] <= 32768).any()
+    check_product(plan, A, B)
+
+
 def test_dense_tier_unsorted_b(plan):
     B = hub_matrix(500, 50000, 7, heavy_rows=set(range(0, 500, 3)), heavy_len=400)
     Bu = gen.random_csr(1, 1, 1.0, 0)  # placeholder for type
