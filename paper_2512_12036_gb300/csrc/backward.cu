@@ -335,11 +335,23 @@ void launch_backward(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     g.opts = p->opts;
     launch_group(p, g, w, w.map, nullptr, s);
     if (m > 0) {
-        if (B.cols <= kBwdDenseCols)
+        // warp-per-row tiers are latency-bound: as many resident blocks as
+        // their shared memory allows
+        auto resident = [&](const void* f, size_t smem) {
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kBwdWarps * 32, smem);
+            return sms * (occ > 0 ? occ : 1);
+        };
+        if (B.cols <= kBwdDenseCols) {
+            const size_t sd = (size_t)kBwdWarps * B.cols * 4;
             SPG_LAUNCH(p, K_BWD, s,
-                       k_bwd_dense<<<sms * 2, kBwdWarps * 32, kBwdWarps * B.cols * 4, s>>>(x, BW_DENSE));
+                       k_bwd_dense<<<resident((const void*)k_bwd_dense, sd), kBwdWarps * 32, sd, s>>>(
+                           x, BW_DENSE));
+        }
+        const size_t sw = (size_t)kBwdWarps * kBwdWarpSlots * 8;
         SPG_LAUNCH(p, K_BWD, s,
-                   k_bwd_warp<<<sms * 2, kBwdWarps * 32, kBwdWarps * kBwdWarpSlots * 8, s>>>(x, BW_WARP));
+                   k_bwd_warp<<<resident((const void*)k_bwd_warp, sw), kBwdWarps * 32, sw, s>>>(
+                       x, BW_WARP));
         SPG_LAUNCH(p, K_BWD, s,
                    k_bwd_block<<<sms, kBwdBlockThreads, kBwdBlockSlots * 8, s>>>(x, BW_BLOCK, 6));
         SPG_LAUNCH(p, K_BWD, s,
