@@ -702,7 +702,8 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
 // per row so that the expected entries of a pass (nnz_row / P per panel)
 // stay within 3/4 of the value array; a pass that still holds more is
 // accumulated in word ranges of at most `cap` entries.
-constexpr int kRankPanels = 16;
+constexpr int kRankPanels = 24;       // 8 and 16 measured slower, 32 leaves too few values
+constexpr int kRankOccUnroll = 8;     // occupancy expansion items are one int
 
 __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, CsrDev B,
                                                                    const int* map, Ctl* ctl,
@@ -798,7 +799,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                 }
             }
             // 1. occupancy
-            expand_tile_padded<kT, float, kD32Unroll>(tile, bs, len, mya, load_key, mark);
+            expand_tile_padded<kT, float, kRankOccUnroll>(tile, bs, len, mya, load_key, mark);
             // 2. word ranks and the pass's columns (thread t owns words [wb, wb + wpt))
             const int nw = (span + 31) >> 5;
             const int wpt = (nw + kT - 1) / kT;
