@@ -9,9 +9,10 @@
 //   colcnt   entries of B per column, then turned into hot flags (0/1),
 //   hot_rank exclusive prefix of the flags (the rank of a hot column),
 //   hot_col  the hot columns in ascending order,
-//   bhot     for every stored entry of B its column's hot rank, or -1,
-// so a kernel learns an entry's hotness with one coalesced load beside
-// col/val.
+//   bhot     for every stored entry of B its column, or for a hot column
+//            (sign bit | hot rank),
+// so the fp64 dense tier reads an entry's column and hotness with one
+// coalesced load beside val.
 #include "internal.h"
 
 namespace spg {
@@ -75,11 +76,14 @@ __global__ void k_hot_cols(const int* flag, const int* rank, int ncols, int* hot
         if (flag[c]) hot_col[rank[c]] = (int)c;
 }
 
+// bhot[j]: B's column j with hot columns replaced by (sign bit | hot rank),
+// and out-of-range columns by INT_MAX (which every column check rejects)
 __global__ void k_bhot(CsrDev B, const int* flag, const int* rank, int* bhot) {
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < B.nnz;
          j += (long long)gridDim.x * blockDim.x) {
         const int c = B.col[j];
-        bhot[j] = ((unsigned)c < (unsigned)B.cols && flag[c]) ? rank[c] : -1;
+        if ((unsigned)c >= (unsigned)B.cols) bhot[j] = 0x7fffffff;
+        else bhot[j] = flag[c] ? (int)(0x80000000u | (unsigned)rank[c]) : c;
     }
 }
 

@@ -96,7 +96,7 @@ struct WsLayout {
     size_t colcnt = 0;       // int32 [B.cols+1]  entries per column of B, then hot flags
     size_t hot_rank = 0;     // int32 [B.cols+1]  exclusive prefix of the hot flags
     size_t hot_col = 0;      // int32 [B.cols]    hot columns in ascending order
-    size_t bhot = 0;         // int32 [B.nnz]     hot rank of each B entry's column, or -1
+    size_t bhot = 0;         // int32 [B.nnz]     each B entry's column, or (sign bit | hot rank)
     bool has_hot = false;
     size_t total = 0;
     int m = 0, nblk = 0, nscan = 0, panels = 0;

@@ -883,16 +883,10 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
 // launch); when it holds more hot columns than kSlots it is split into
 // sub-passes at hot-column boundaries (re-reading its segments).
 constexpr int kHotThreads = 1024;
-constexpr int kHotUnroll = 2;      // products per warp step batch (4 and 8 measured slower)
+constexpr int kHotUnroll = 4;      // products per warp step batch (2 and 8 measured slower)
 constexpr int kHotSlots = 1024;
 constexpr int kHotCopies = 8;
 static_assert(kHotThreads / kHotCopies <= 160, "a copy must gather at most 160 terms per tile");
-
-struct KeyValHot {
-    int key;
-    float v;
-    int hot;
-};
 
 __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrDev B,
                                                                   const int* map, Ctl* ctl,
@@ -911,11 +905,13 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
     unsigned* bm = reinterpret_cast<unsigned*>(st + W);               // [W / 32]
     __shared__ int s_idx;
     __shared__ int scratch[33];
+    __shared__ unsigned touched[kHotSlots / 32];  // hot slots that received a product this sub-pass
     __shared__ ExpandTile<kHotThreads, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
     if (begin >= end) return;
     const int t = threadIdx.x;
     const int nwords = W >> 5;
+    for (int i = t; i < kHotSlots / 32; i += kHotThreads) touched[i] = 0u;
     for (int i = t; i < W; i += kHotThreads) st[i] = 0.f;
     for (int i = t; i < nwords; i += kHotThreads) bm[i] = 0u;
     for (int i = t; i < kHotSlots; i += kHotThreads) acc[i] = 0.0;
@@ -925,33 +921,39 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
     const int npass = (P + ppp - 1) / ppp;
     const long long stride = P + 1;
 
-    int pc0 = 0, lo = 0, hi = 0, hr0 = 0;                 // pass start, sub-pass [lo, hi)
-    auto load = [&](int q) { return KeyValHot{B.col[q], B.val[q], bhot[q]}; };
-    auto apply = [&](KeyValHot kv, float a, int seg) {
-        if (!key_in(kv.key, B, ctl)) return;
-        if (kv.key < lo || kv.key >= hi) {
-            if (use_tab && (kv.key < pc0 || kv.key >= pc0 + W)) set_status(ctl, ST_INTERNAL);
-            return;
-        }
-        const int kk = kv.key - pc0;
-        atomicOr(&bm[kk >> 5], 1u << (kk & 31));
-        if (kv.hot >= 0) {
-            const int slot = kv.hot - hr0;
-            if ((unsigned)slot >= (unsigned)kHotSlots) {
-                set_status(ctl, ST_INTERNAL);
-            } else if (split) {
-                atomicAdd(&cp[(seg & (kHotCopies - 1)) * kHotSlots + slot], a * kv.v);
-            } else {
-                atomicAdd(&acc[slot], (double)a * (double)kv.v);
+    // pass start, sub-pass columns [lo, hi), its hot ranks [hr0, hr0 + nhs),
+    // and the pass's hot ranks [hrp0, hrp1)
+    int pc0 = 0, lo = 0, hi = 0, hr0 = 0, nhs = 0, hrp0 = 0, hrp1 = 0;
+    auto load = [&](int q) { return KeyVal{bhot[q], B.val[q]}; };
+    // one bitmap OR and one fp32 add per product, hot or cold, on selected
+    // addresses (a hot product marks its slot, a cold one its column), so the
+    // warp does not diverge into two instruction sequences
+    auto apply = [&](KeyVal kv, float a, int seg) {
+        const int code = kv.key;
+        const bool hot = code < 0;                   // (sign bit | hot rank)
+        int x;                                       // hot slot or pass column
+        if (hot) {
+            const int rank = code & 0x7fffffff;
+            x = rank - hr0;
+            if ((unsigned)x >= (unsigned)nhs) {      // another sub-pass's column
+                if (use_tab && (rank < hrp0 || rank >= hrp1)) set_status(ctl, ST_INTERNAL);
+                return;
             }
         } else {
-            atomicAdd(&st[kk], a * kv.v);
+            if (!key_in(code, B, ctl)) return;
+            if (code < lo || code >= hi) {
+                if (use_tab && (code < pc0 || code >= pc0 + W)) set_status(ctl, ST_INTERNAL);
+                return;
+            }
+            x = code - pc0;
         }
+        atomicOr((hot ? touched : bm) + (x >> 5), 1u << (x & 31));
+        if (hot && !split) atomicAdd(&acc[x], (double)a * (double)kv.v);
+        else atomicAdd(hot ? &cp[(seg & (kHotCopies - 1)) * kHotSlots + x] : &st[x], a * kv.v);
     };
     // add the copies of this sub-pass's hot slots into the fp64 accumulator
     auto fold = [&]() {
-        const int nh = hot_rank[hi] - hr0;
-        for (int h = t; h < nh; h += kHotThreads) {
+        for (int h = t; h < nhs; h += kHotThreads) {
             double v = acc[h];
 #pragma unroll
             for (int c = 0; c < kHotCopies; ++c) {
@@ -1008,14 +1010,20 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                     len = nxt - cur;
                 }
             }
+            hrp0 = hot_rank[pc0];
+            hrp1 = hot_rank[pc1];
             // sub-passes of at most kHotSlots hot columns
             for (lo = pc0; lo < pc1; lo = hi) {
                 hr0 = hot_rank[lo];
-                const int hr_end = hot_rank[pc1];
-                hi = hr_end - hr0 <= kHotSlots ? pc1 : hot_col[hr0 + kHotSlots];
+                hi = hrp1 - hr0 <= kHotSlots ? pc1 : hot_col[hr0 + kHotSlots];
                 if (hi <= lo || hi > pc1) {              // defensive: malformed hot data
                     set_status(ctl, ST_INTERNAL);
                     hi = pc1;
+                }
+                nhs = hot_rank[hi] - hr0;
+                if (nhs < 0 || nhs > kHotSlots) {        // defensive: malformed hot data
+                    set_status(ctl, ST_INTERNAL);
+                    nhs = nhs < 0 ? 0 : kHotSlots;
                 }
                 if (cached) {
                     // packed expansion: this tier's per-pass segments are often short
@@ -1047,14 +1055,19 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                         fold();
                     }
                 }
-                // round the hot columns' sums once into the pass array
-                const int nh = hot_rank[hi] - hr0;
-                for (int h = t; h < nh; h += kHotThreads) {
+                // round the hot columns' sums once into the pass array and mark
+                // the hot columns that received a product in the bitmap
+                for (int h = t; h < nhs; h += kHotThreads) {
                     const int kk = hot_col[hr0 + h] - pc0;
-                    if ((unsigned)kk < (unsigned)W) st[kk] = (float)acc[h];
+                    if ((unsigned)kk < (unsigned)W) {
+                        st[kk] = (float)acc[h];
+                        if ((touched[h >> 5] >> (h & 31)) & 1u) atomicOr(&bm[kk >> 5], 1u << (kk & 31));
+                    }
                     acc[h] = 0.0;
                 }
                 __syncthreads();
+                // (emit_bitmap synchronises before the next sub-pass's products)
+                if (t < kHotSlots / 32) touched[t] = 0u;
                 // emit [lo, hi) in column order (bits outside it are clear)
                 written += emit_bitmap<kHotThreads>(
                     bm, (lo - pc0) >> 5, (hi - pc0 + 31) >> 5, pc0, colC, valC, out, written,
