@@ -447,7 +447,12 @@ __device__ __forceinline__ void expand_walk(const Off* off, const int* sbsv, con
                     const int rel = (int)d;      // lane 0: <= 0, then non-decreasing
                     const int wbs = e < nE ? sbsv[e] : 0;
                     const Acc wa = e < nE ? sav[e] : Acc(0);
-                    const int src = warp_find_src(rel, lane);
+                    // segments are non-empty, so their starts inside the
+                    // window are distinct: lane l's segment is the number
+                    // of starts at or before position l
+                    const unsigned starts =
+                        __reduce_or_sync(kFull, rel > 0 && rel < 32 ? 1u << rel : 0u);
+                    const int src = __popc(starts & ((2u << lane) - 1u));
                     tq[u] = __shfl_sync(kFull, wbs, src) + (lane - __shfl_sync(kFull, rel, src));
                     aq[u] = __shfl_sync(kFull, wa, src);
                     sq[u] = s + src;

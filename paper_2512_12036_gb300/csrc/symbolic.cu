@@ -14,7 +14,7 @@
 
 namespace spg {
 
-constexpr int kSymDenseUnroll = 4;   // products per warp step batch (2 measured slower)
+constexpr int kSymDenseUnroll = 6;   // products per warp step batch (4 and 8 measured slower)
 
 constexpr int kSymDenseWords = 48 * 1024;   // 192 KB bitmap (1.5M columns per pass)
 
