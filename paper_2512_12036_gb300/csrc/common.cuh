@@ -453,7 +453,7 @@ __device__ __forceinline__ void expand_walk(const Off* off, const int* sbsv, con
                     const unsigned starts =
                         __reduce_or_sync(kFull, rel > 0 && rel < 32 ? 1u << rel : 0u);
                     const int src = __popc(starts & ((2u << lane) - 1u));
-                    tq[u] = __shfl_sync(kFull, wbs, src) + (lane - __shfl_sync(kFull, rel, src));
+                    tq[u] = __shfl_sync(kFull, wbs - rel, src) + lane;
                     aq[u] = __shfl_sync(kFull, wa, src);
                     sq[u] = s + src;
                     vq[u] = base + lane < wend;
