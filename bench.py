@@ -171,10 +171,10 @@ class ClockSampler:
 # DRAM bytes (read + write) per intermediate product of the dense accumulation
 # kernels, from one ncu capture of the kernel as it stands (row sample 1 in
 # 128 of the R-MAT scale 20 workload, right operand and L2 pressure as in the
-# full case; summary and command in profiles/dense_tiers_rmat20_rows1in128.md).
+# full case; the summary and its command are kept under profiles/).
 # Scaled by the full workload's products of the tier to give the per-launch
 # traffic; a kernel changed since its capture must drop out of this table.
-DRAM_BYTES_PER_PRODUCT = {"num_dense64": (793.911040e6 + 331.378e6) / 256228740}
+DRAM_BYTES_PER_PRODUCT = {"num_dense64": (493.976064e6 + 335.917e6) / 256228740}
 
 
 def max_over_ranks(x: float, device) -> float:
