@@ -172,8 +172,9 @@ __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, Csr
         int rs, re;
         row_extent(A, row, rs, re, ctl);
         int nnz = 0;
-        for (long long c0 = 0; c0 < B.cols; c0 += span_max) {
-            const int span = (int)(B.cols - c0 < span_max ? B.cols - c0 : span_max);
+        for (long long c0l = 0; c0l < B.cols; c0l += span_max) {
+            const int c0 = (int)c0l;                  // below B.cols, so it fits
+            const int span = (int)(B.cols - c0l < span_max ? B.cols - c0l : span_max);
             const int nw = (span + 31) >> 5;
             for (int q = threadIdx.x; q < nw; q += blockDim.x) bm[q] = 0u;
             __syncthreads();
@@ -183,8 +184,8 @@ __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, Csr
                 [&](int t) { return B.col[t]; },
                 [&](int key, float) {
                     if (!key_ok(key, B, ctl)) return;
-                    const long long kk = key - c0;
-                    if (kk < 0 || kk >= span) return;
+                    const int kk = key - c0;          // both in [0, B.cols)
+                    if ((unsigned)kk >= (unsigned)span) return;
                     atomicOr(&bm[kk >> 5], 1u << (kk & 31));
                 });
             int cnt = 0;
