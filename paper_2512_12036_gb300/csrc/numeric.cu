@@ -731,18 +731,22 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
 
     int c0 = 0, span = 0, lo = 0, hi = 0, rbase = 0;
     auto load_key = [&](int q) { return B.col[q]; };
+    // [c0, c0 + span) by one unsigned compare; columns outside B never fall
+    // in it and are flagged on the slow side
     auto mark = [&](int key, float) {
-        if (!key_in(key, B, ctl)) return;
-        const int kk = key - c0;
-        if ((unsigned)kk < (unsigned)span) atomicOr(&bm[kk >> 5], 1u << (kk & 31));
-        else set_status(ctl, ST_INTERNAL);
+        const unsigned kk = (unsigned)key - (unsigned)c0;
+        if (kk < (unsigned)span) atomicOr(&bm[kk >> 5], 1u << (kk & 31));
+        else if (key_in(key, B, ctl)) set_status(ctl, ST_INTERNAL);
     };
     auto load = [&](int q) { return KeyVal{B.col[q], B.val[q]}; };
     auto add = [&](KeyVal kv, float a) {
-        if (!key_in(kv.key, B, ctl)) return;
-        const int kk = kv.key - c0;
-        const int w = kk >> 5;
-        if ((unsigned)kk >= (unsigned)span || w < lo || w >= hi) return;   // other word range
+        const unsigned kk = (unsigned)kv.key - (unsigned)c0;
+        if (kk >= (unsigned)span) {
+            key_in(kv.key, B, ctl);
+            return;
+        }
+        const int w = (int)(kk >> 5);
+        if ((unsigned)(w - lo) >= (unsigned)(hi - lo)) return;            // other word range
         const int r = rk[w] + __popc(bm[w] & ((1u << (kk & 31)) - 1u)) - rbase;
         if ((unsigned)r < (unsigned)cap) atomicAdd(&vals[r], a * kv.v);
         else set_status(ctl, ST_INTERNAL);
@@ -940,9 +944,11 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                 return;
             }
         } else {
-            if (!key_in(code, B, ctl)) return;
-            if (code < lo || code >= hi) {
-                if (use_tab && (code < pc0 || code >= pc0 + W)) set_status(ctl, ST_INTERNAL);
+            // [lo, hi) by one unsigned compare; a column outside B never
+            // falls in it and is flagged here
+            if ((unsigned)code - (unsigned)lo >= (unsigned)(hi - lo)) {
+                if (key_in(code, B, ctl) && use_tab && (code < pc0 || code >= pc0 + W))
+                    set_status(ctl, ST_INTERNAL);
                 return;
             }
             x = code - pc0;

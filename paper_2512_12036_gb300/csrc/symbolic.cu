@@ -183,10 +183,11 @@ __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, Csr
                 [&](int j, int& bs, int& len, float&) { a_entry(A, B, j, bs, len, ctl); },
                 [&](int t) { return B.col[t]; },
                 [&](int key, float) {
-                    if (!key_ok(key, B, ctl)) return;
-                    const int kk = key - c0;          // both in [0, B.cols)
-                    if ((unsigned)kk >= (unsigned)span) return;
-                    atomicOr(&bm[kk >> 5], 1u << (kk & 31));
+                    // one unsigned compare: in [c0, c0 + span) or not (a column
+                    // outside B never is; it is flagged on the slow side)
+                    const unsigned kk = (unsigned)key - (unsigned)c0;
+                    if (kk < (unsigned)span) atomicOr(&bm[kk >> 5], 1u << (kk & 31));
+                    else key_ok(key, B, ctl);
                 });
             int cnt = 0;
             for (int q = threadIdx.x; q < nw; q += blockDim.x) cnt += __popc(bm[q]);
