@@ -174,7 +174,7 @@ class ClockSampler:
 # full case; the summary and its command are kept under profiles/).
 # Scaled by the full workload's products of the tier to give the per-launch
 # traffic; a kernel changed since its capture must drop out of this table.
-DRAM_BYTES_PER_PRODUCT = {"num_dense64": (493.976064e6 + 335.917e6) / 256228740}
+DRAM_BYTES_PER_PRODUCT = {"num_dense64": (493.987072e6 + 335.559e6) / 256228740}
 
 
 def max_over_ranks(x: float, device) -> float:
