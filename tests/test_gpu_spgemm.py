@@ -376,6 +376,40 @@ def test_row_view_input(plan):
     compare(C, ref)
 
 
+@pytest.mark.parametrize("bad", ["past_last_column", "negative"])
+def test_malformed_column_in_dense_tiers(bad):
+    # a column outside B on the hub rows of B, read by rows of both dense
+    # accumulation tiers (the rank-compacted fp32 kernel and the fp64
+    # hot-column kernel, through the panel table and the column words):
+    # reported as ERR_INVALID, no fault, and the plan stays usable. The
+    # corrupted entries keep their rows sorted, so the sorted-B paths run.
+    opts = {"panel_cols": 1024, "block_max_nnz": 512, "block_max_ip": 1024,
+            "fp32_max_terms": 40}
+    A = gen.rmat_symmetric(12, 16, seed=5)
+    na = np.diff(A.row_ptr.astype(np.int64))
+    ip, _ = oracle.ip_count(A, A)
+    nnz = oracle.symbolic(A, A)
+    dense = (nnz > opts["block_max_nnz"]) & ~((ip <= 32) & (na <= 32))
+    f64 = (na > opts["fp32_max_terms"]) & (ip > opts["fp32_max_terms"])
+    hubs = np.argsort(na)[-5:]                       # the five hub rows
+    reads_hub = np.zeros(A.rows, bool)
+    reads_hub[np.repeat(np.arange(A.rows), na)[np.isin(A.col, hubs)]] = True
+    assert (dense & f64 & reads_hub).sum() > 0 and (dense & ~f64 & reads_hub).sum() > 0
+    B = gen.HostCSR(A.rows, A.cols, A.row_ptr, A.col.copy(), A.val)
+    for k in hubs:
+        s, e = int(A.row_ptr[k]), int(A.row_ptr[k + 1])
+        if bad == "negative":
+            B.col[s] = -1
+        else:
+            B.col[e - 1] = A.cols + 7
+    plan = Plan(**opts)
+    with pytest.raises(SpgemmError) as e:
+        plan.spgemm(DeviceCSR.from_host(A), DeviceCSR.from_host(B))
+    assert e.value.code == _lib.ERR_INVALID
+    torch.cuda.synchronize()
+    check_product(plan, A, A)
+
+
 def test_structure_deterministic(plan):
     A = gen.rmat_symmetric(12, 8, seed=8)
     c1 = run(plan, A, A)
