@@ -76,11 +76,21 @@ def workload_name(scale: int, row_stride: int = 1) -> str:
 # CPU oracle baseline (rank 0 only): a bounded random sample of rows of A*A.
 # ---------------------------------------------------------------------------
 
+def host_threads() -> int:
+    """Host cores this process may run on. The oracle is timed with all of
+    them: rank 0 runs it alone (other ranks do no CPU work meanwhile), and
+    torchrun's default OMP_NUM_THREADS=1 must not shrink it."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(A, seconds: float, seed: int = 0):
     import oracle
     rng = np.random.default_rng(seed)
     ip, _ = oracle.ip_count(A, A)
-    cores = oracle.max_threads()
+    cores = host_threads()
     # calibrate on a small sample, then size the main one to ~`seconds`
     order = rng.permutation(A.rows).astype(np.int32)
     csum = np.cumsum(ip[order])
@@ -91,13 +101,13 @@ def cpu_baseline(A, seconds: float, seed: int = 0):
 
     cal = take(2e7)
     t0 = time.perf_counter()
-    oracle.spgemm(A, A, rows=cal, with_bound=False)
+    oracle.spgemm(A, A, rows=cal, nthreads=cores, with_bound=False)
     t_cal = max(time.perf_counter() - t0, 1e-3)
     rate = float(ip[cal].sum()) / t_cal
     rows = take(rate * seconds)
     prods = float(ip[rows].sum())
     t0 = time.perf_counter()
-    oracle.spgemm(A, A, rows=rows, with_bound=False)
+    oracle.spgemm(A, A, rows=rows, nthreads=cores, with_bound=False)
     t = time.perf_counter() - t0
     return {"value": 2 * prods / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{rows.size} uniformly drawn rows of A*A ({prods:.3e} intermediate "
@@ -719,7 +729,7 @@ def run_reference(args):
     import oracle
     A_h, _, _, _ = workload(args.scale)
     ip, _ = oracle.ip_count(A_h, A_h)
-    cores = oracle.max_threads()
+    cores = host_threads()
     rng = np.random.default_rng(1)
     # each step: a fresh uniformly drawn sample of ~1e8 intermediate products
     target = 1e8 if args.scale >= 18 else 1e7
@@ -729,11 +739,11 @@ def run_reference(args):
         k = int(np.searchsorted(np.cumsum(ip[order]), target)) + 1
         samples.append(order[:k])
     for r in samples[:args.warmup]:
-        oracle.spgemm(A_h, A_h, rows=r, with_bound=False)
+        oracle.spgemm(A_h, A_h, rows=r, nthreads=cores, with_bound=False)
     prods = 0.0
     t0 = time.perf_counter()
     for r in samples[args.warmup:]:
-        oracle.spgemm(A_h, A_h, rows=r, with_bound=False)
+        oracle.spgemm(A_h, A_h, rows=r, nthreads=cores, with_bound=False)
         prods += float(ip[r].sum())
     t = time.perf_counter() - t0
     value = 2 * prods / t / 1e9
