@@ -220,6 +220,63 @@ def test_row_subset_matches_full():
         assert np.array_equal(C.val[a], S.val[b])
 
 
+def test_contraction_sums_over_clusters():
+    # S^T A S with S an assignment matrix (Alg. 7): entry (p, q) is the sum of
+    # A over the pairs (i, j) with cluster(i) = p, cluster(j) = q, stored
+    # exactly where such a pair holds a stored entry of A (explicit zeros
+    # too), and the total of A is preserved. Small-integer values keep every
+    # sum exact in fp32 and fp64, so the chain S^T A -> fp32 -> (S^T A) S is
+    # compared exactly against a cluster-label scatter.
+    A = gen.rmat_symmetric(10, 8, seed=4)
+    vals = np.random.default_rng(6).integers(0, 9, size=A.col.size).astype(np.float32)
+    A = gen.HostCSR(A.rows, A.cols, A.row_ptr, A.col, vals)
+    m = 40
+    S = gen.assignment_matrix(A.rows, m, seed=5)
+    lab = S.col.astype(np.int64)
+    T = oracle.spgemm(gen.transpose_structure(S), A)
+    Th = gen.HostCSR(T.rows, T.cols, T.row_ptr.astype(np.int32), T.col,
+                     T.val.astype(np.float32))
+    C = oracle.spgemm(Th, S)
+    r = np.repeat(np.arange(A.rows), np.diff(A.row_ptr.astype(np.int64)))
+    D = np.zeros((m, m))
+    np.add.at(D, (lab[r], lab[A.col]), vals.astype(np.float64))
+    P = np.zeros((m, m), dtype=bool)
+    P[lab[r], lab[A.col]] = True
+    assert np.array_equal(oracle_dense(C), D)
+    assert np.array_equal(np.diff(C.row_ptr), P.sum(axis=1))
+    Cr = np.repeat(np.arange(C.rows), np.diff(C.row_ptr))
+    assert P[Cr, C.col].all()
+    assert C.val.sum() == float(vals.astype(np.float64).sum())
+
+
+def test_block_diagonal_is_per_block_products():
+    # rows of C depend only on their own row of A: the product of two
+    # block-diagonal operands is the block-diagonal of the per-block products,
+    # column offsets included, bit for bit (same terms in the same order)
+    A1, B1 = gen.random_csr(30, 40, 0.2, seed=21), gen.random_csr(40, 50, 0.15, seed=22)
+    A2, B2 = gen.random_csr(20, 35, 0.25, seed=23), gen.random_csr(35, 60, 0.1, seed=24)
+
+    def sp_of(X):
+        return sp.csr_matrix((X.val, X.col, X.row_ptr), shape=(X.rows, X.cols))
+
+    def host_of(M):
+        M = sp.csr_matrix(M)
+        M.sort_indices()
+        return gen.HostCSR(M.shape[0], M.shape[1], M.indptr.astype(np.int32),
+                           M.indices.astype(np.int32), M.data.astype(np.float32))
+
+    A = host_of(sp.block_diag([sp_of(A1), sp_of(A2)], format="csr"))
+    B = host_of(sp.block_diag([sp_of(B1), sp_of(B2)], format="csr"))
+    C = oracle.spgemm(A, B)
+    for (r0, c0), Cb in (((0, 0), oracle.spgemm(A1, B1)), ((30, 50), oracle.spgemm(A2, B2))):
+        for i in range(Cb.rows):
+            a = slice(C.row_ptr[r0 + i], C.row_ptr[r0 + i + 1])
+            b = slice(Cb.row_ptr[i], Cb.row_ptr[i + 1])
+            assert np.array_equal(C.col[a], Cb.col[b] + c0)
+            assert np.array_equal(C.val[a], Cb.val[b])
+            assert np.array_equal(C.bound[a], Cb.bound[b])
+
+
 def test_thread_count_does_not_change_result():
     A = gen.rmat_symmetric(10, 8, seed=3)
     C1 = oracle.spgemm(A, A, nthreads=1)
