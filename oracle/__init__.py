@@ -22,8 +22,10 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# ORACLE_C_SOURCE names another copy of oracle.c, built next to that copy:
+# the mutation test uses it to check that the pins catch planted mistakes
+_SRC = os.environ.get("ORACLE_C_SOURCE") or os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(_SRC)), "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
