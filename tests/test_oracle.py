@@ -335,8 +335,22 @@ def test_mcl_step_against_brute_force(order):
     rng = np.random.default_rng(4 + order)
     M = gen.random_csr(40, 40, 0.4, seed=31 + order)
     M.val[:] = (rng.random(M.nnz) * 0.01).astype(np.float32)   # many below theta
-    theta, k, r = 2e-3, 5, 2.0
+    k, r = 5, 2.0
+    # row 0 holds one value whose (inflated, for order 1) fp32 decision value
+    # equals theta exactly: values below theta are removed, that one stays
+    s0 = slice(M.row_ptr[0], M.row_ptr[1])
+    assert M.row_ptr[1] - M.row_ptr[0] >= 3
+    if order == 0:
+        theta = float(np.float32(2e-3))
+        edge = np.float32(theta)
+    else:
+        edge = np.float32(0.05)
+        theta = float(np.float32(np.float64(edge) ** r))
+    row0 = np.full(M.row_ptr[1] - M.row_ptr[0], 1e-4, np.float32)
+    row0[0], row0[1] = edge, np.float32(0.08)
+    M.val[s0] = row0
     out = oracle.mcl_step(M, theta, k, r, order)
+    assert M.col[M.row_ptr[0]] in out.col[out.row_ptr[0]:out.row_ptr[1]].tolist()
     for i in range(M.rows):
         cols, vals = M.row(i)
         dec = vals if order == 0 else (vals.astype(np.float64) ** r).astype(np.float32)

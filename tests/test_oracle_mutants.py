@@ -1,7 +1,9 @@
 """The oracle's pins catch plausible mistakes: each case plants one mistake
 in a copy of oracle.c (a dropped factor, an overwrite instead of a sum, an
 off-by-one in the product count, a signed error scale, a wrong operand in
-either gradient) and runs the pin tests against it; every mutant must fail
+either gradient, repeated columns counted twice, an inclusive prune
+threshold, top-k keeping the smallest, no inflation, no normalisation) and
+runs the pin tests against it; every mutant must fail
 them, and the unmodified copy must pass. CPU only."""
 import os
 import subprocess
@@ -21,6 +23,15 @@ MUTANTS = {
     "dA_wrong_operand": ("acc += g[c] * (double)valB[t];", "acc += g[c] * (double)valA[j];"),
     "dB_wrong_operand": ("if (dB) dB[t] += (double)valA[j] * g[c];",
                          "if (dB) dB[t] += (double)valB[t] * g[c];"),
+    "symbolic_counts_repeats": ("if (seen[c] != (int64_t)r) { seen[c] = (int64_t)r; ++nnz; }",
+                                "{ seen[c] = (int64_t)r; ++nnz; }"),
+    "mcl_prune_inclusive": ("if (decide < (float)theta) continue;",
+                            "if (decide <= (float)theta) continue;"),
+    "mcl_topk_keeps_smallest": ("if (x[0] > y[0]) return -1;\n    if (x[0] < y[0]) return 1;",
+                                "if (x[0] < y[0]) return -1;\n    if (x[0] > y[0]) return 1;"),
+    "mcl_no_inflation": ("double w = pow(v, r);", "double w = v;"),
+    "normalise_unscaled": ("out[q] = s > 0 ? (double)val[q] / s : 0.0;",
+                           "out[q] = (double)val[q];"),
 }
 
 
