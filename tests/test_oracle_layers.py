@@ -75,6 +75,18 @@ def test_forward_without_pruning_is_plain_product():
     np.testing.assert_allclose(C, A @ X.astype(np.float64), rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("k", [1, 4])
+def test_forward_with_pruning_is_masked_product(k):
+    # Eq. 1 with Eq. 2's mask taken from a plain Python sort of each row
+    A, X, W, _ = _problem()
+    Y, C, M = layers.layer_forward(A, X, W, k=k)
+    Mb = brute_topk_mask(X, k)
+    assert np.array_equal(M, Mb) and (M.sum(axis=1) == k).all()
+    T = np.where(Mb, X.astype(np.float64), 0.0)
+    np.testing.assert_allclose(C, A @ T, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(Y, A @ T @ W, rtol=1e-12, atol=1e-12)
+
+
 def test_backward_matches_autograd():
     A, X, W, dY = _problem()
     k = 4

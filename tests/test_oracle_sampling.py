@@ -48,6 +48,28 @@ def test_weighted_draws_match_plain_loop(mode):
         assert (np.diff(out_col[out_rp[i]:out_rp[i + 1]]) > 0).all()
 
 
+def test_boundary_draws_skip_zero_and_negative_weights():
+    # the draw is the first entry whose running weight exceeds u * total, so
+    # a draw landing exactly on a boundary skips the zero-weight entries
+    # there, and mode 1 weighs by max(value, 0): a negative value is never
+    # drawn (mode 2 squares it: drawable). Values and uniforms are exact in
+    # fp32 and fp64.
+    rows = [([0.0, 0.0, 0.5, 0.0, 1.0], 0.0, 1, 2),     # u = 0: first positive weight
+            ([1.0, 0.0, 1.0, 0.5], 0.4, 1, 2),          # target 1.0 = running weight of 0 and 1
+            ([-1.0, 0.5, 0.5, 0.25], 0.0, 1, 1),        # negative weight clamped to 0
+            ([-1.0, 0.5, 0.5, 0.25], 0.5, 2, 0)]        # mode 2: weights 1, .25, .25, .0625
+    for w, u, mode, want in rows:
+        val = np.array(w, np.float32)
+        wt = val.astype(np.float64)
+        wt = wt * wt if mode == 2 else np.maximum(wt, 0.0)
+        assert brute_draw(wt, u) == want
+        rp = np.array([0, val.size])
+        col = np.arange(val.size)
+        out_rp, out_col, _, _ = sampling.sample_rows(rp, col, val, 1, np.array([[u]], np.float32),
+                                                     mode)
+        assert out_col.tolist() == [want], (w, u, mode)
+
+
 def test_equal_weights_reduce_to_uniform():
     rp, col, _ = random_rows(80, 60, seed=4)
     ones = np.ones(col.size, np.float32)
