@@ -870,11 +870,13 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
 // Heavy rows whose entries can gather more than fp32_max_terms products
 // (the fp64 tier). Products on cold columns of B (see hot.cu) are summed in
 // fp32 exactly as in the fp32 tier. Products on hot columns (one slot per
-// hot column of the sub-pass) are split over kCopies fp32 partial sums by
-// the rank of their A entry in the expansion tile (rank mod kCopies): with
-// at most kHotThreads entries in a tile and each entry adding at most one
-// product to a column (B rows sorted, no repeated column), a copy gathers
-// at most kHotThreads / kCopies = 128 terms per column. After every tile
+// hot column of the sub-pass) are split over kHotCopies fp32 partial sums
+// by the rank of their A entry in the expansion tile (rank mod kHotCopies):
+// with at most kHotThreads entries in a tile and each entry adding at most
+// one product to a column (B rows sorted, no repeated column), a copy
+// gathers at most kHotThreads / kHotCopies = 128 terms per column. A
+// product reads B's column word (the column, or sign bit | hot rank for a
+// hot column) beside its value. After every tile
 // the copies are added into an fp64 accumulator in a fixed order and
 // cleared; at the end of the sub-pass the accumulator is rounded once into
 // the pass array. The error stays within (gamma_128 + u) * sum|a||b| plus
@@ -884,7 +886,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
 // accumulator with fp64 atomics instead.
 //
 // A pass covers ppp table panels (as many as shared memory holds, set at
-// launch); when it holds more hot columns than kSlots it is split into
+// launch); when it holds more hot columns than kHotSlots it is split into
 // sub-passes at hot-column boundaries (re-reading its segments).
 constexpr int kHotThreads = 1024;
 constexpr int kHotUnroll = 4;      // products per warp step batch (2 and 8 measured slower)
