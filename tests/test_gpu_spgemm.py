@@ -410,6 +410,39 @@ def test_malformed_column_in_dense_tiers(bad):
     check_product(plan, A, A)
 
 
+@pytest.mark.parametrize("unsorted", [False, True])
+def test_dense_tiers_without_panel_table(unsorted):
+    # B with 1.1M columns is wider than 1024 panels of 1024 columns, so there
+    # is no panel table: heavy rows run the dense kernels that filter whole B
+    # rows pass by pass (the fp32 dense-array kernel and the fp64 group
+    # kernel), with sorted and with unsorted rows of B
+    opts = {"panel_cols": 1024, "block_max_nnz": 512, "block_max_ip": 1024,
+            "fp32_max_terms": 40}
+    rng = np.random.default_rng(101)
+    k, n, m = 2000, 1_100_000, 200
+    r, c = [], []
+    for i in range(k):
+        cc = np.unique(rng.integers(0, n, size=int(rng.integers(0, 61))))
+        r.append(np.full(cc.size, i))
+        c.append(rng.permutation(cc) if unsorted else cc)
+    B = gen.csr_from_coo(k, n, np.concatenate(r), np.concatenate(c),
+                         gen.uniform_open_closed(rng, sum(x.size for x in c)))
+    if unsorted:
+        B = gen.HostCSR(k, n, B.row_ptr, np.concatenate(c).astype(np.int32), B.val)
+    lens = [150] * 5 + [30] * 20 + [int(x) for x in rng.integers(0, 5, size=m - 25)]
+    ra = np.concatenate([np.full(d, i) for i, d in enumerate(lens)])
+    ca = np.concatenate([np.sort(rng.choice(k, size=d, replace=False)) for d in lens])
+    A = gen.csr_from_coo(m, k, ra, ca, gen.uniform_open_closed(rng, ra.size))
+    assert -(-n // opts["panel_cols"]) > 1024
+    na = np.diff(A.row_ptr)
+    ip, _ = oracle.ip_count(A, B)
+    nnz = oracle.symbolic(A, B)
+    dense = nnz > opts["block_max_nnz"]
+    f64 = (na > opts["fp32_max_terms"]) & (ip > opts["fp32_max_terms"])
+    assert (dense & f64).sum() == 5 and (dense & ~f64).sum() >= 15
+    check_product(Plan(**opts), A, B)
+
+
 def test_structure_deterministic(plan):
     A = gen.rmat_symmetric(12, 8, seed=8)
     c1 = run(plan, A, A)
