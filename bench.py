@@ -109,9 +109,19 @@ def cpu_baseline(A, seconds: float, seed: int = 0):
     t0 = time.perf_counter()
     oracle.spgemm(A, A, rows=rows, nthreads=cores, with_bound=False)
     t = time.perf_counter() - t0
+    # the same oracle on one thread, over a sample 1/cores as large (about the
+    # same wall time)
+    rows1 = take(rate * seconds / max(cores, 1))
+    prods1 = float(ip[rows1].sum())
+    t0 = time.perf_counter()
+    oracle.spgemm(A, A, rows=rows1, nthreads=1, with_bound=False)
+    t1 = time.perf_counter() - t0
     return {"value": 2 * prods / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{rows.size} uniformly drawn rows of A*A ({prods:.3e} intermediate "
-                      f"products, {t:.1f} s), fp64 dense accumulator, OpenMP over rows"}
+                      f"products, {t:.1f} s), fp64 dense accumulator, OpenMP over rows",
+            "single_thread": {"value": 2 * prods1 / t1 / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": f"the first {rows1.size} of the same rows "
+                                        f"({prods1:.3e} products, {t1:.1f} s)"}}
 
 
 # ---------------------------------------------------------------------------
