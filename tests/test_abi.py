@@ -28,3 +28,30 @@ def test_invalid_arguments_rejected_without_gpu():
     assert L.spgemm_plan_create(None, None, 0) == _lib.ERR_INVALID
     n = ctypes.c_size_t()
     assert L.spgemm_workspace_bytes(None, None, None, ctypes.byref(n)) == _lib.ERR_INVALID
+
+
+def test_every_entry_point_rejects_null_arguments():
+    # NULL pointers and zero sizes everywhere: each status-returning call
+    # reports ERR_INVALID before touching a device (destroying a NULL plan is
+    # a no-op), so a caller's mistake never reaches a kernel
+    L = _lib.lib()
+    skip = {"spgemm_status_string", "spgemm_kernel_count", "spgemm_kernel_name",
+            "spgemm_launch_total"}
+    for name, (res, args) in _lib.PROTOTYPES.items():
+        if name in skip:
+            continue
+        vals = []
+        for a in args:
+            if a in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t):
+                vals.append(0)
+            elif a is ctypes.c_float:
+                vals.append(0.0)
+            elif a is _lib.ALLOC_FN:
+                vals.append(_lib.ALLOC_FN())
+            else:
+                vals.append(None)
+        rc = getattr(L, name)(*vals)
+        want = _lib.OK if name == "spgemm_plan_destroy" else _lib.ERR_INVALID
+        assert rc == want, (name, rc)
+    assert L.spgemm_launch_total(None) == 0
+    assert L.spgemm_kernel_count() > 0 and L.spgemm_kernel_name(0)
