@@ -55,3 +55,18 @@ def test_every_entry_point_rejects_null_arguments():
         assert rc == want, (name, rc)
     assert L.spgemm_launch_total(None) == 0
     assert L.spgemm_kernel_count() > 0 and L.spgemm_kernel_name(0)
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    # the product path has no CPU fallback: without CUDA, making a plan or
+    # moving a matrix to the device fails loudly
+    import pytest
+    import torch
+
+    from paper_2512_12036_gb300 import DeviceCSR, Plan, gen
+    if torch.cuda.is_available():
+        pytest.skip("checks the behaviour of a machine without a GPU")
+    with pytest.raises(Exception):
+        Plan()
+    with pytest.raises(Exception):
+        DeviceCSR.from_host(gen.erdos_renyi(10, 2, seed=1))
