@@ -153,10 +153,13 @@ int spgemm_row_ptr(const spgemm_plan* plan, const int32_t* row_nnz, int32_t n, v
  *  - n <= 2^26 (67,108,864) rows, else SPGEMM_ERR_UNSUPPORTED before any work;
  *  - the calling thread's current device must be the plan's device;
  *  - the first call on each device looks up the scratch's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture;
- *  - every call shares the one scratch array, so calls that overlap on the
- *    GPU (different streams, threads or processes' streams) race: order
- *    them on one stream or serialise them.
+ *    (cudaGetSymbolAddress), and so does the first call after the device's
+ *    context changes (cudaDeviceReset, a new primary context); make such a
+ *    call before any stream capture;
+ *  - within one process every call on a device shares the one scratch
+ *    array, so calls that overlap on the GPU (different streams or host
+ *    threads) race: order them on one stream or serialise them. Separate
+ *    processes each get their own copy of the array.
  * total [out, host, nullable]: as for spgemm_row_ptr (non-NULL synchronises
  * and returns SPGEMM_ERR_OVERFLOW past INT32_MAX). */
 int spgemm_row_ptr_static(const spgemm_plan* plan, const int32_t* row_nnz, int32_t n,

@@ -26,18 +26,54 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
+// Per device: the scratch's device address and the id of the context it was
+// looked up in. A device reset (cudaDeviceReset) or a new primary context
+// reloads the module, and the symbol may then sit at another address, so the
+// address is looked up again whenever the current context's id changes.
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
 
-// Device address of the scratch on the current device (looked up once per
-// device; the lookup must not happen inside a stream capture).
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Id of the calling thread's current context (unique for the life of the
+// process, unlike the context handle, which a new context may reuse);
+// 0 when the driver cannot say.
+unsigned long long current_context_id() {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) !=
+                cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess)
+            return 0;
+        g_ctx_get_current = (CtxGetCurrentFn)f1;
+        g_ctx_get_id = (CtxGetIdFn)f2;
+    }
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != 0 || ctx == nullptr || g_ctx_get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch on the current device, looked up on the
+// first call in each context (the lookup must not happen inside a stream
+// capture).
 int scratch_address(int device, void** out) {
     if (device < 0 || device >= kMaxDevices) return SPGEMM_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[device]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[device] || ctx == 0 || ctx != g_scratch_ctx[device]) {
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || ptr == nullptr)
             return SPGEMM_ERR_CUDA;
         g_scratch_addr[device] = ptr;
+        g_scratch_ctx[device] = ctx;
     }
     *out = g_scratch_addr[device];
     return SPGEMM_OK;

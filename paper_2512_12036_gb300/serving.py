@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from ._lib import ERR_BUDGET
+from ._lib import ERR_BUDGET, ERR_TIMEOUT
 
 
 @dataclass
@@ -115,15 +115,22 @@ class Server:
                 for q in self.slot_q:
                     q.put(None)
                 return
-            req.bound, req.ip = self.bound_fn(req)
-            parts = [req]
-            if req.bound > self.limit:
-                parts = self.split_fn(req, self.limit) if self.split_fn else None
-                if not parts or any(p.bound > self.limit for p in parts):
-                    req.error = ERR_BUDGET
-                    req.done = time.perf_counter()
-                    req.event.set()
-                    continue
+            try:
+                req.bound, req.ip = self.bound_fn(req)
+                parts = [req]
+                if req.bound > self.limit:
+                    parts = self.split_fn(req, self.limit) if self.split_fn else None
+                    if not parts or any(p.bound > self.limit for p in parts):
+                        parts = None
+                        req.error = ERR_BUDGET
+            except Exception as exc:  # noqa: BLE001 - reported on the request
+                parts = None
+                req.error = getattr(exc, "code", -1) or -1
+            if parts is None:
+                req.done = time.perf_counter()
+                req.event.set()
+                continue
+            if len(parts) > 1 or parts[0] is not req:
                 req.parts = parts
                 req.pending = len(parts)
                 for p in parts:
@@ -247,12 +254,17 @@ def gpu_server(slots: int = 4, budget_bytes: int = 64 << 30, device: int = 0,
             count_plan.workspace_init(ws)
             ip_row = count_arena.take(8 * max(req.A.rows, 1), torch.int64)[:req.A.rows]
             ip_row, ip_total = count_plan.count(req.A, req.B, ws, ip_row=ip_row)
-        req.ip_row = ip_row.clone() if req.A.rows else ip_row
-        return request_bound(count_plan, req.A, req.B, nws, ip_total), ip_total
+            bound = request_bound(count_plan, req.A, req.B, nws, ip_total)
+            # the per-row counts are needed only to split a request that does
+            # not fit a slot; they go to host memory (on the count stream,
+            # before the next request reuses the arena), never to a new
+            # device buffer
+            req.ip_row = ip_row.cpu().numpy() if bound > per_slot else None
+        return bound, ip_total
 
     def split_fn(req, budget):
         """Blocks of consecutive rows whose bounds fit half an arena."""
-        ip = req.ip_row.cpu().numpy()
+        ip = req.ip_row
         cols = int(req.B.cols)
         csum = np.cumsum(np.minimum(ip, cols) * 8 + 16)
         target = budget // 2
@@ -323,16 +335,21 @@ def run_plain(reqs, arrivals, device: int = 0, max_block_nnz: int = 2**31 - 1):
     return reqs
 
 
-def run_served(server: Server, reqs, arrivals):
-    """Submit requests at the given arrival offsets (seconds) and wait."""
+def run_served(server: Server, reqs, arrivals, timeout_s: float = 600.0):
+    """Submit requests at the given arrival offsets (seconds) and wait, at
+    most ``timeout_s`` after the last submission; a request still unfinished
+    then is marked failed (ERR_TIMEOUT) instead of blocking the caller."""
     t0 = time.perf_counter()
     for req, at in zip(reqs, arrivals):
         now = time.perf_counter() - t0
         if now < at:
             time.sleep(at - now)
         server.submit(req)
+    deadline = time.perf_counter() + timeout_s
     for req in reqs:
-        req.event.wait()
+        if not req.event.wait(max(0.0, deadline - time.perf_counter())):
+            req.error = ERR_TIMEOUT
+            req.done = time.perf_counter()
     return reqs
 
 

@@ -89,3 +89,49 @@ def test_oversize_request_split_into_parts():
     assert big.error == 0 and sorted(big.result) == [(q, 40) for q in range(4)]
     assert small.error == 0 and huge.error == ERR_BUDGET
     assert srv.adm.peak <= 50
+
+
+def test_bound_or_split_failure_is_reported_and_dispatch_continues():
+    """A bound or split function that raises fails that request only; the
+    dispatcher keeps serving the requests after it."""
+    class BoundError(RuntimeError):
+        code = 4
+
+    def bound_fn(req):
+        if req.A == "bad-bound":
+            raise BoundError("arena exhausted")
+        if req.A == "bad-split":
+            return 1000, 0
+        return 10, 0
+
+    def split_fn(req, limit):
+        raise MemoryError("cannot split")
+
+    srv = serving.Server(bound_fn, lambda slot, req: req.A, slots=2, budget_bytes=100,
+                         split_fn=split_fn, request_limit=50)
+    names = ["a", "bad-bound", "b", "bad-split", "c"]
+    reqs = [srv.submit(serving.Request(A=n, B=None)) for n in names]
+    for r in reqs:
+        assert r.event.wait(5)
+    srv.close()
+    assert [r.error for r in reqs] == [0, 4, 0, -1, 0]
+    assert [r.result for r in reqs if not r.error] == ["a", "b", "c"]
+    assert srv.adm.used == 0
+
+
+def test_run_served_marks_stuck_requests_instead_of_hanging():
+    from paper_2512_12036_gb300._lib import ERR_TIMEOUT
+    gate = threading.Event()
+
+    def exec_fn(slot, req):
+        gate.wait(10)
+        return req.A
+
+    srv = serving.Server(lambda r: (1, 0), exec_fn, slots=1, budget_bytes=10)
+    reqs = [serving.Request(A=i, B=None) for i in range(2)]
+    t0 = time.perf_counter()
+    serving.run_served(srv, reqs, [0.0, 0.0], timeout_s=0.2)
+    assert time.perf_counter() - t0 < 5
+    assert all(r.error == ERR_TIMEOUT for r in reqs)
+    gate.set()
+    srv.close()
