@@ -49,7 +49,7 @@ def parse():
                     help="skip the batched / served / MCL pattern measurements")
     ap.add_argument("--gnn-graphs", type=int, default=8192)
     ap.add_argument("--panel-cols", type=int, default=None)
-    ap.add_argument("--served-requests", type=int, default=32)
+    ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--row-stride", type=int, default=1,
                     help="left operand of A*A = every k-th row of A (a smaller case with the "
                          "same row mix and the full right operand, for profiling; not the "
@@ -400,125 +400,269 @@ def pattern_sampling(A, device, minibatches: int = 64, batch: int = 1024, fanout
     return out
 
 
-def pattern_served(n_requests: int, device, A_big=None, S_big=None, St_big=None):
-    """Mixed requests (R-MAT / ER A*B with n log-uniform in [1e3, 1e6] and
-    degree U[4, 32], an MCL expansion M*M, graph contraction S^T A) arriving
-    as a Poisson process at 0.8x the plain path's measured capacity; served
-    by the continuous-batching loop (4 slots, 64 GB budget) vs the plain
-    per-request path on the same arrivals."""
-    import torch
-
-    from paper_2512_12036_gb300 import DeviceCSR, Plan, gen, serving
-
-    rng = np.random.default_rng(6)
+def served_pool(device, pairs: int, seed: int = 6):
+    """Distinct request operands for the mixed-size serving pattern: n
+    log-uniform in [1e3, 1e6], Erdos-Renyi or R-MAT (50/50), average degree
+    U[4, 32], B independent of A (same n and generator, next seed)."""
+    from paper_2512_12036_gb300 import DeviceCSR, gen
+    rng = np.random.default_rng(seed)
     pool = []
-    for q in range(6):
+    for q in range(pairs):
         n = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
         d = float(rng.uniform(4, 32))
-        if q % 2:
-            Ah = gen.erdos_renyi(n, d, seed=600 + q)
-            Bh = gen.erdos_renyi(n, d, seed=601 + q)
-        else:
-            sc = int(np.ceil(np.log2(n)))
-            Ah = gen.rmat_symmetric(sc, max(1, int(round(d / 2))), seed=600 + q)
-            Bh = gen.rmat_symmetric(sc, max(1, int(round(d / 2))), seed=601 + q)
-        pool.append((f"{'er' if q % 2 else 'rmat'}_n{Ah.rows}_d{d:.0f}",
-                     DeviceCSR.from_host(Ah, device), DeviceCSR.from_host(Bh, device)))
-    M = gen.rmat_symmetric(16, 8, seed=4, self_loops=True)
-    Md = DeviceCSR.from_host(M, device)
-    from paper_2512_12036_gb300.mcl import normalise_rows
-    Mn = normalise_rows(Plan(device=device.index), Md)
-    pool.append(("mcl_expand_rmat16", Mn, Mn))
-    if St_big is not None:
-        pool.append(("contract_StA_rmat20", St_big, A_big))
+        kind = "rmat" if rng.random() < 0.5 else "er"
+        make = gen.rmat_graph if kind == "rmat" else gen.erdos_renyi
+        Ah = make(n, d, seed=1000 + 2 * q)
+        Bh = make(n, d, seed=1001 + 2 * q)
+        pool.append((f"{kind}_n{n}_d{d:.0f}", DeviceCSR.from_host(Ah, device),
+                     DeviceCSR.from_host(Bh, device), Ah, Bh))
+    return pool
+
+
+def pattern_served(n_requests: int, device, pairs: int = 24, loads=(0.5, 0.8)):
+    """Mixed-size serving: `n_requests` A*B requests drawn from a pool of
+    `pairs` distinct operand pairs (served_pool), arriving as a Poisson
+    process at each load (a fraction of the plain path's measured
+    capacity), then all at once (burst). The continuous-batching loop
+    (4 slots, 64 GB budget, admission by the product-count bound) against
+    the plain per-request path (one request at a time, C allocated per
+    call) on the same arrivals; accuracy: one served result per pool pair
+    against the oracle on sampled rows."""
+    import torch
+
+    import oracle
+    from paper_2512_12036_gb300 import Plan, serving
+
+    t0 = time.perf_counter()
+    pool = served_pool(device, pairs)
+    gen_s = time.perf_counter() - t0
+    rng = np.random.default_rng(6)
     picks = rng.integers(0, len(pool), size=n_requests)
 
     def make():
         return [serving.Request(A=pool[i][1], B=pool[i][2], tag=pool[i][0]) for i in picks]
 
-    # plain capacity: mean service time of the pool, back to back
     plan = Plan(device=device.index)
-    svc = []
-    for tag, Ad, Bd in pool:
+    svc, ips = [], []
+    for _, Ad, Bd, _, _ in pool:            # warm, then the service time of each pair
+        plan.spgemm_blocks(Ad, Bd)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        blocks, ip_t, _ = plan.spgemm_blocks(Ad, Bd)
-        torch.cuda.synchronize()
-        svc.append(time.perf_counter() - t0)
-        del blocks
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            blocks, ip_t, _ = plan.spgemm_blocks(Ad, Bd)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            del blocks
+        svc.append(min(ts))
+        ips.append(ip_t)
     mean_svc = float(np.mean([svc[i] for i in picks]))
-    rate = 0.8 / mean_svc
-    arrivals = serving.poisson_arrivals(n_requests, rate, seed=7)
-    plain = make()
-    t0 = time.perf_counter()
-    for req, at in zip(plain, arrivals):
-        now = time.perf_counter() - t0
-        if now < at:
-            time.sleep(at - now)
-        req.arrival = t0 + at
-        blocks, req.ip, _ = plan.spgemm_blocks(req.A, req.B)
-        torch.cuda.synchronize()
-        del blocks
-        req.done = time.perf_counter()
-    plain_wall = time.perf_counter() - t0
+    gflop = 2.0 * sum(ips[i] for i in picks) / 1e9
+
+    def run_plain(reqs, arrivals):
+        t0 = time.perf_counter()
+        for req, at in zip(reqs, arrivals):
+            now = time.perf_counter() - t0
+            if now < at:
+                time.sleep(at - now)
+            req.arrival = t0 + at
+            blocks, req.ip, _ = plan.spgemm_blocks(req.A, req.B)
+            torch.cuda.synchronize()
+            del blocks
+            req.done = time.perf_counter()
+        return time.perf_counter() - t0
+
     srv = serving.gpu_server(slots=4, budget_bytes=64 << 30, device=device.index,
                              keep_results=False)
-    served = make()
-    t0 = time.perf_counter()
-    serving.run_served(srv, served, arrivals)
-    served_wall = time.perf_counter() - t0
-    # saturation: the same requests all arriving at once (maximum throughput)
-    burst_served = make()
-    t0 = time.perf_counter()
-    serving.run_served(srv, burst_served, np.zeros(n_requests))
-    burst_served_wall = time.perf_counter() - t0
-    srv.close()
-    burst_plain = make()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for req in burst_plain:
-        req.arrival = t0
-        blocks, req.ip, _ = plan.spgemm_blocks(req.A, req.B)
-        torch.cuda.synchronize()
-        del blocks
-        req.done = time.perf_counter()
-    burst_plain_wall = time.perf_counter() - t0
-    errs = [r.error for r in served if r.error]
-    gflop = 2.0 * sum(r.ip for r in plain) / 1e9
-    ps, ss = serving.latency_stats(plain), serving.latency_stats(served)
-    return {"requests": n_requests, "pool": [t for t, _, _ in pool],
-            "arrival_rate_per_s": rate, "load": 0.8,
-            "plain": {**ps, "gflops": gflop / plain_wall},
-            "served": {**ss, "gflops": gflop / served_wall, "slots": 4, "budget_gb": 64,
-                       "peak_admitted_gb": srv.adm.peak / 2**30, "errors": len(errs)},
-            "burst_plain": {**serving.latency_stats(burst_plain),
-                            "gflops": gflop / burst_plain_wall},
-            "burst_served": {**serving.latency_stats(burst_served),
-                             "gflops": gflop / burst_served_wall}}
+    out = {"requests": n_requests, "pool_pairs": len(pool), "pool": [p[0] for p in pool],
+           "generate_s": round(gen_s, 1), "plain_capacity_rps": 1.0 / mean_svc,
+           "gflop_total": gflop}
+    try:
+        for load in loads:
+            rate = load / mean_svc
+            arrivals = serving.poisson_arrivals(n_requests, rate, seed=7)
+            plain = make()
+            wall_p = run_plain(plain, arrivals)
+            served = make()
+            t0 = time.perf_counter()
+            serving.run_served(srv, served, arrivals)
+            wall_s = time.perf_counter() - t0
+            out[f"load_{load}"] = {
+                "arrival_rate_per_s": rate,
+                "plain": {**serving.latency_stats(plain), "gflops": gflop / wall_p},
+                "served": {**serving.latency_stats(served), "gflops": gflop / wall_s,
+                           "errors": sum(1 for r in served if r.error)}}
+        burst_p = make()
+        wall_p = run_plain(burst_p, np.zeros(n_requests))
+        burst_s = make()
+        t0 = time.perf_counter()
+        serving.run_served(srv, burst_s, np.zeros(n_requests))
+        wall_s = time.perf_counter() - t0
+        out["burst"] = {"plain": {**serving.latency_stats(burst_p), "gflops": gflop / wall_p},
+                        "served": {**serving.latency_stats(burst_s), "gflops": gflop / wall_s,
+                                   "errors": sum(1 for r in burst_s if r.error)}}
+        out["served_peak_admitted_gb"] = srv.adm.peak / 2**30
+    finally:
+        srv.close()
+    # accuracy: one served result per pool pair, sampled rows against the oracle
+    vsrv = serving.gpu_server(slots=4, budget_bytes=64 << 30, device=device.index,
+                              keep_results=True)
+    worst, checked = 0.0, 0
+    try:
+        reqs = [serving.Request(A=p[1], B=p[2], tag=p[0]) for p in pool]
+        serving.run_served(vsrv, reqs, np.zeros(len(reqs)))
+        for req, (_, _, _, Ah, Bh) in zip(reqs, pool):
+            if req.error:
+                raise RuntimeError(f"served request {req.tag} failed ({req.error})")
+            parts = req.result if isinstance(req.result, list) else [req.result]
+            sub = req.parts if isinstance(req.result, list) else [req]
+            rr = np.random.default_rng(checked)
+            for part, C in zip(sub, parts):
+                rows = np.unique(rr.integers(0, C.rows, size=min(C.rows, 500)))
+                ref = oracle.spgemm(Ah, Bh, rows=rows + part.row_begin)
+                rp = C.row_ptr.cpu().numpy().astype(np.int64)
+                col, val = C.col.cpu().numpy(), C.val.cpu().numpy()
+                gc = np.concatenate([col[rp[i]:rp[i + 1]] for i in rows])
+                gv = np.concatenate([val[rp[i]:rp[i + 1]] for i in rows]).astype(np.float64)
+                assert np.array_equal(np.diff(ref.row_ptr), rp[rows + 1] - rp[rows])
+                assert np.array_equal(gc, ref.col)
+                err = np.abs(gv - ref.val) / np.where(ref.bound > 0, ref.bound, 1.0)
+                assert (err <= 1e-5).all(), f"served {req.tag}: value outside tolerance"
+                worst = max(worst, float(err.max(initial=0.0)))
+            checked += 1
+    finally:
+        vsrv.close()
+    out["accuracy"] = {"pairs_checked": checked, "rows_per_pair": "<= 500 sampled",
+                       "max_err_over_bound": worst, "tolerance": 1e-5}
+    return out
 
 
-def pattern_mcl(device, iterations: int = 20):
+def pattern_mcl(device, iterations: int = 20, jobs: int = 4):
     """Markov clustering on R-MAT scale 18, edge factor 8, symmetrised, with
     self-loops: 20 iterations of expansion, prune < 1e-4, top-32, inflation 2,
-    renormalisation."""
+    renormalisation. Plain (one spgemm call per expansion) and served (every
+    expansion a request to the continuous-batching server, the loop's
+    operands staying on the device); the two must give the same clustering.
+    Then `jobs` independent clusterings (seeds 4, 5, ...) back to back on
+    the plain path against all of them at once through the server."""
+    import threading
+
     import torch
 
-    from paper_2512_12036_gb300 import DeviceCSR, Plan, gen
-    from paper_2512_12036_gb300.mcl import markov_cluster
+    from paper_2512_12036_gb300 import DeviceCSR, Plan, gen, serving
+    from paper_2512_12036_gb300.mcl import markov_cluster, markov_cluster_served
 
-    G = gen.rmat_symmetric(18, 8, seed=4, self_loops=True)
-    Gd = DeviceCSR.from_host(G, device)
+    graphs = [DeviceCSR.from_host(gen.rmat_symmetric(18, 8, seed=4 + j, self_loops=True), device)
+              for j in range(jobs)]
     plan = Plan(device=device.index)
-    markov_cluster(plan, Gd, iterations=1)
+    markov_cluster(plan, graphs[0], iterations=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = markov_cluster(plan, Gd, iterations=iterations)
+    res = markov_cluster(plan, graphs[0], iterations=iterations)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     ip = sum(res.ip_history)
-    return {"workload": "rmat18_ef8_selfloops_mcl", "iterations": iterations, "seconds": dt,
-            "expansion_gflops": 2.0 * ip / dt / 1e9, "ip_first": res.ip_history[0],
-            "nnz_final": res.nnz_history[-1]}
+    srv = serving.gpu_server(slots=4, budget_bytes=64 << 30, device=device.index,
+                             keep_results=True)
+    try:
+        markov_cluster_served(srv, plan, graphs[0], iterations=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res_s, reqs = markov_cluster_served(srv, plan, graphs[0], iterations=iterations)
+        torch.cuda.synchronize()
+        dt_s = time.perf_counter() - t0
+        same = (res_s.ip_history == res.ip_history and res_s.nnz_history == res.nnz_history)
+        a, b = res_s.Mt.to_host(), res.Mt.to_host()
+        same = same and np.array_equal(a.col, b.col) and np.array_equal(a.row_ptr, b.row_ptr)
+        # several independent clusterings: plain back to back vs all at once
+        plans = [Plan(device=device.index) for _ in range(jobs)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ip_jobs = 0
+        for j in range(jobs):
+            ip_jobs += sum(markov_cluster(plans[j], graphs[j], iterations=iterations).ip_history)
+        torch.cuda.synchronize()
+        dt_jobs_plain = time.perf_counter() - t0
+        out = [None] * jobs
+
+        def client(j):
+            with torch.cuda.stream(torch.cuda.Stream(device=device)):
+                out[j] = markov_cluster_served(srv, plans[j], graphs[j], iterations=iterations,
+                                               tag=f"job{j}")
+
+        ths = [threading.Thread(target=client, args=(j,)) for j in range(jobs)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        torch.cuda.synchronize()
+        dt_jobs_served = time.perf_counter() - t0
+        job_lat = [r.latency for o in out if o for r in o[1]]
+    finally:
+        srv.close()
+    lat = [r.latency for r in reqs]
+    return {"workload": "rmat18_ef8_selfloops_mcl", "iterations": iterations,
+            "ip_first": res.ip_history[0], "nnz_final": res.nnz_history[-1],
+            "plain": {"seconds": dt, "expansion_gflops": 2.0 * ip / dt / 1e9},
+            "served": {"seconds": dt_s, "expansion_gflops": 2.0 * ip / dt_s / 1e9,
+                       "expansion_p50_ms": 1e3 * _pct(lat, 0.5),
+                       "expansion_p99_ms": 1e3 * _pct(lat, 0.99),
+                       "same_clustering_as_plain": bool(same)},
+            "concurrent_jobs": {"jobs": jobs, "plain_seconds": dt_jobs_plain,
+                                "served_seconds": dt_jobs_served,
+                                "plain_gflops": 2.0 * ip_jobs / dt_jobs_plain / 1e9,
+                                "served_gflops": 2.0 * ip_jobs / dt_jobs_served / 1e9,
+                                "served_expansion_p50_ms": 1e3 * _pct(job_lat, 0.5),
+                                "served_expansion_p99_ms": 1e3 * _pct(job_lat, 0.99),
+                                "all_ok": all(o is not None for o in out)}}
+
+
+def pattern_er4096(device, reps: int = 50):
+    """C = A*A for a 4096 x 4096 Erdos-Renyi adjacency (average degree 8,
+    seed 1, fp32 U(0,1], no self-loops): latency of one plain call through
+    the public API (C allocated by the call, the result's size read back)
+    and of the device-resident form (buffers reused, no host sync inside),
+    against the oracle on the host cores."""
+    import torch
+
+    import oracle
+    from paper_2512_12036_gb300 import DeviceCSR, Plan, gen
+
+    A_h = gen.erdos_renyi(4096, 8, seed=1)
+    A = DeviceCSR.from_host(A_h, device)
+    plan = Plan(device=device.index)
+    ws = plan.workspace(A, A)
+    C = plan.spgemm(A, A, ws=ws)
+    blocks, ip, nnz = plan.spgemm_blocks(A, A, ws=ws)
+    torch.cuda.synchronize()
+    lat = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        C = plan.spgemm(A, A, ws=ws)
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - t0)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.spgemm_blocks(A, A, ws=ws, out=blocks)
+    e1.record(stream)
+    e1.synchronize()
+    dev_ms = e0.elapsed_time(e1) / reps
+    t0 = time.perf_counter()
+    for _ in range(5):
+        oracle.spgemm(A_h, A_h, nthreads=host_threads(), with_bound=False)
+    cpu_ms = 1e3 * (time.perf_counter() - t0) / 5
+    ref = oracle.spgemm(A_h, A_h)
+    Ch = C.to_host()
+    ok = (np.array_equal(Ch.row_ptr.astype(np.int64), ref.row_ptr) and np.array_equal(Ch.col, ref.col)
+          and bool((np.abs(Ch.val.astype(np.float64) - ref.val) <= 1e-5 * ref.bound).all()))
+    return {"workload": "er4096_deg8_AxA", "ip": int(ip), "nnz_C": int(nnz),
+            "plain_call_p50_ms": 1e3 * _pct(lat, 0.5), "plain_call_p99_ms": 1e3 * _pct(lat, 0.99),
+            "device_resident_ms": dev_ms, "device_resident_gflops": 2.0 * ip / (dev_ms / 1e3) / 1e9,
+            "oracle_ms": cpu_ms, "oracle_cores": host_threads(), "matches_oracle": ok}
 
 
 def run_ours(args):
@@ -690,11 +834,13 @@ def run_ours(args):
         del blocks
         torch.cuda.empty_cache()
         patterns = {}
-        patterns["served"] = pattern_served(args.served_requests, dev, A, S, St)
+        patterns["served"] = pattern_served(args.served_requests, dev)
         torch.cuda.empty_cache()
         patterns["batched_gnn"] = pattern_batched(args.gnn_graphs, dev)
         torch.cuda.empty_cache()
         patterns["mcl"] = pattern_mcl(dev)
+        torch.cuda.empty_cache()
+        patterns["er4096"] = pattern_er4096(dev)
         torch.cuda.empty_cache()
         patterns["bulk_sampling"] = pattern_sampling(A, dev)
 

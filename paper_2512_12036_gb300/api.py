@@ -262,12 +262,15 @@ class Plan:
 
     # ------------------------------------------------------------ whole product
     def spgemm(self, A: DeviceCSR, B: DeviceCSR, ws: torch.Tensor | None = None,
-               stream=None) -> DeviceCSR:
-        """C = A*B through the one-call entry point (C allocated by torch)."""
+               stream=None, ip_row: torch.Tensor | None = None) -> DeviceCSR:
+        """C = A*B through the one-call entry point (C allocated by torch).
+        ``ip_row`` (int64, A.rows, on the device) receives the per-row
+        intermediate-product counts of the call (Algorithm 1) when given."""
         if ws is None:
             ws = self.workspace(A, B)
         dev = A.device
-        ip_row = torch.empty(A.rows, dtype=torch.int64, device=dev)
+        if ip_row is None:
+            ip_row = torch.empty(A.rows, dtype=torch.int64, device=dev)
         row_nnz = torch.empty(A.rows, dtype=torch.int32, device=dev)
         row_ptr = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
         keep = {}

@@ -167,6 +167,38 @@ def rmat_symmetric(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.1
     return _undirected_to_csr(n, lo, hi, w, loops)
 
 
+def rmat_graph(n: int, avg_degree: float, seed: int, a: float = 0.57, b: float = 0.19,
+               c: float = 0.19) -> HostCSR:
+    """Symmetric R-MAT graph on exactly n vertices with about ``avg_degree``
+    stored entries per row: n * avg_degree / 2 directed R-MAT edges at scale
+    ceil(log2 n), every edge with an endpoint >= n drawn again (from the
+    same generator) until all lie below n; then as rmat_symmetric (labels
+    permuted, self-loops dropped, symmetrised, deduplicated, U(0,1] values)."""
+    if n <= 1:
+        return csr_from_coo(n, n, np.zeros(0), np.zeros(0), np.zeros(0))
+    scale = max(1, int(np.ceil(np.log2(n))))
+    rng = np.random.default_rng(seed)
+    ne = max(1, int(round(n * avg_degree / 2)))
+    ab, abc = a + b, a + b + c
+    u = np.zeros(0, dtype=np.int64)
+    v = np.zeros(0, dtype=np.int64)
+    while u.size < ne:
+        m = ne - u.size
+        uu = np.zeros(m, dtype=np.int64)
+        vv = np.zeros(m, dtype=np.int64)
+        for level in range(scale):
+            r = rng.random(m, dtype=np.float32)
+            bit = np.int64(1) << (scale - 1 - level)
+            uu += (r >= ab).astype(np.int64) * bit
+            vv += (((r >= a) & (r < ab)) | (r >= abc)).astype(np.int64) * bit
+        keep = (uu < n) & (vv < n)
+        u = np.concatenate([u, uu[keep]])
+        v = np.concatenate([v, vv[keep]])
+    perm = rng.permutation(n).astype(np.int64)
+    lo, hi = _unique_pairs(n, perm[u], perm[v])
+    return _undirected_to_csr(n, lo, hi, uniform_open_closed(rng, lo.size))
+
+
 def assignment_matrix(n: int, m: int, seed: int) -> HostCSR:
     """S (n x m): row r holds a single 1.0 at a uniformly drawn cluster id."""
     rng = np.random.default_rng(seed)

@@ -52,17 +52,60 @@ class MCLResult:
 def markov_cluster(plan: Plan, Gt: DeviceCSR, iterations: int = 20, theta: float = 1e-4,
                    k: int = 32, r: float = 2.0, order: int = 0) -> MCLResult:
     """Gt: the graph with self-loops added, as M^T (rows = columns of M).
-    A fixed number of iterations replaces the convergence test."""
+    A fixed number of iterations replaces the convergence test. Each
+    expansion is one spgemm call (its own count, allocation and
+    accumulation phases); the per-row product counts it writes are summed
+    on the device and read once at the end."""
     M = normalise_rows(plan, Gt)
-    nnz_hist, ip_hist = [M.nnz], []
+    nnz_hist, ip_sums = [M.nnz], []
     for _ in range(iterations):
-        ws = plan.workspace(M, M)
-        ip, ip_total = plan.count(M, M, ws)
-        E = plan.spgemm(M, M)
-        ip_hist.append(ip_total)
+        ip_row = torch.empty(M.rows, dtype=torch.int64, device=M.device)
+        E = plan.spgemm(M, M, ip_row=ip_row)
+        ip_sums.append(ip_row.sum())
         M = mcl_step(plan, E, theta, k, r, order)
         nnz_hist.append(M.nnz)
+    ip_hist = [int(x) for x in torch.stack(ip_sums).cpu()] if ip_sums else []
     return MCLResult(M, iterations, nnz_hist, ip_hist)
+
+
+def markov_cluster_served(server, plan: Plan, Gt: DeviceCSR, iterations: int = 20,
+                          theta: float = 1e-4, k: int = 32, r: float = 2.0, order: int = 0,
+                          tag: str = "mcl"):
+    """markov_cluster with every expansion M*M submitted as a request to a
+    continuous-batching server (serving.gpu_server with keep_results=True),
+    so the expansions of several clustering jobs, or of other clients,
+    share the device. Returns (MCLResult, the expansion requests)."""
+    from .serving import Request
+
+    M = normalise_rows(plan, Gt)
+    nnz_hist, ip_hist, reqs = [M.nnz], [], []
+    for it in range(iterations):
+        req = server.submit(Request(A=M, B=M, tag=f"{tag}_expand{it}"))
+        req.event.wait()
+        if req.error:
+            raise _lib.SpgemmError(req.error if req.error > 0 else _lib.ERR_INTERNAL,
+                                   f"served MCL expansion {it}")
+        E = req.result if not isinstance(req.result, list) else _stack_blocks(req.result, M)
+        ip_hist.append(req.ip)
+        reqs.append(req)
+        M = mcl_step(plan, E, theta, k, r, order)
+        nnz_hist.append(M.nnz)
+    return MCLResult(M, iterations, nnz_hist, ip_hist), reqs
+
+
+def _stack_blocks(parts, M: DeviceCSR) -> DeviceCSR:
+    """One DeviceCSR from a split request's row blocks (in row order)."""
+    rps, cols, vals, base = [], [], [], 0
+    for q, C in enumerate(parts):
+        rp = C.row_ptr.to(torch.int64) + base
+        rps.append(rp if q == len(parts) - 1 else rp[:-1])
+        cols.append(C.col)
+        vals.append(C.val)
+        base += C.nnz
+    if base > 2**31 - 1:
+        raise _lib.SpgemmError(_lib.ERR_OVERFLOW, "served MCL expansion")
+    return DeviceCSR(M.rows, M.cols, torch.cat(rps).to(torch.int32), torch.cat(cols),
+                     torch.cat(vals))
 
 
 def interpret(Mt: DeviceCSR) -> np.ndarray:

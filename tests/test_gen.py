@@ -101,3 +101,22 @@ def test_split_rows_respects_limit():
             assert min(sums) >= int(counts.sum()) / need - int(counts.max())
     with pytest.raises(ValueError):
         split_rows(counts, 10)
+
+
+def test_rmat_graph_exact_n():
+    for n, d, seed in ((1000, 8.0, 1), (3000, 20.0, 2), (1025, 4.0, 3)):
+        A = gen.rmat_graph(n, d, seed=seed)
+        assert A.rows == A.cols == n
+        rows = np.repeat(np.arange(n), np.diff(A.row_ptr.astype(np.int64)))
+        assert (A.col < n).all() and (A.col >= 0).all()
+        assert not (rows == A.col).any()                     # no self-loops
+        key = rows * n + A.col
+        assert (np.diff(key) > 0).all()                      # sorted, no duplicates
+        back = set(zip(A.col.tolist(), rows.tolist()))
+        assert back == set(zip(rows.tolist(), A.col.tolist()))   # symmetric
+        assert 0.5 * d <= A.nnz / n <= d                     # duplicates merged
+        assert (A.val > 0).all() and (A.val <= 1).all()
+        deg = np.diff(A.row_ptr)
+        assert deg.max() > 4 * deg.mean()                    # skewed like R-MAT
+    a, b = gen.rmat_graph(2000, 8, seed=5), gen.rmat_graph(2000, 8, seed=5)
+    assert np.array_equal(a.col, b.col) and np.array_equal(a.val, b.val)

@@ -1,6 +1,7 @@
 """GPU parity at the benchmark's full size: C = A*A for the R-MAT scale 20
 matrix (ef 16, seed 2; nnz(C) = 2.38e10, produced in even row blocks of at
-most 2^31-1 entries, as the benchmark runs it) and the contraction S^T*A.
+most 2^31-1 entries, as the benchmark runs it) and both products of the
+contraction S^T*A*S (Algorithm 7).
 
 Checked against the oracle: every row's entry count (the oracle's full
 allocation phase, exact), and columns and values of sampled rows (the
@@ -12,6 +13,7 @@ import torch
 
 import oracle
 from paper_2512_12036_gb300 import DeviceCSR, Plan, gen
+from contraction import assignment_labels, label_scatter
 from parity import compare
 
 pytestmark = pytest.mark.gpu
@@ -85,3 +87,24 @@ def test_rmat20_full_size_parity():
     rows = sample_rows(ipt, St_h.rows, seed=2)
     compare(rows_of_blocks(T_blocks, rows), oracle.spgemm(St_h, A_h, rows=rows),
             rows=np.arange(rows.size))
+
+    # second product (S^T A) * S, as the benchmark runs it: sampled rows
+    # against the oracle on the first product's actual output, and every
+    # entry against A's entries scattered by cluster labels (fp64)
+    assert len(T_blocks) == 1
+    T = T_blocks[0][2]
+    S = DeviceCSR.from_host(S_h)
+    C2_blocks, _, nnz2 = plan.spgemm_blocks(T, S)
+    torch.cuda.synchronize()
+    assert len(C2_blocks) == 1
+    T_h = T.to_host()
+    C2_h = C2_blocks[0][2].to_host()
+    ip2, _ = oracle.ip_count(T_h, S_h)
+    rows = sample_rows(ip2, T_h.rows, seed=3)
+    compare(rows_of_blocks(C2_blocks, rows), oracle.spgemm(T_h, S_h, rows=rows),
+            rows=np.arange(rows.size))
+    rp, col, val, absum = label_scatter(A_h, assignment_labels(S_h), clusters)
+    assert nnz2 == col.size
+    assert np.array_equal(C2_h.row_ptr.astype(np.int64), rp)
+    assert np.array_equal(C2_h.col, col)
+    assert (np.abs(C2_h.val.astype(np.float64) - val) <= 2e-5 * absum).all()

@@ -63,3 +63,32 @@ def test_mcl_step_long_rows_and_ties():
         got = mcl_step(plan, DeviceCSR.from_host(E), 1e-4, 32, 2.0, order).to_host()
         ref = oracle.mcl_step(E, 1e-4, 32, 2.0, order)
         assert np.array_equal(got.col, ref.col) and ulp_close(got.val, ref.val)
+
+
+def test_mcl_expansions_served_match_plain_and_oracle():
+    """Markov clustering with every expansion a request to the continuous-
+    batching server: each served expansion against the oracle on its own
+    input, and the clustering after three iterations against the plain
+    (one spgemm call per expansion) run."""
+    from paper_2512_12036_gb300 import serving
+    from paper_2512_12036_gb300.mcl import markov_cluster, markov_cluster_served
+
+    plan = Plan()
+    G = graph(11, 8, seed=5)
+    Gd = DeviceCSR.from_host(G)
+    srv = serving.gpu_server(slots=2, budget_bytes=1 << 30, keep_results=True,
+                             count_ws_bytes=64 << 20, max_rows=1 << 16)
+    try:
+        res_s, reqs = markov_cluster_served(srv, plan, Gd, iterations=3)
+    finally:
+        srv.close()
+    assert len(reqs) == 3 and all(r.error == 0 for r in reqs)
+    for req in reqs:
+        Mh = req.A.to_host()
+        compare(req.result.to_host(), oracle.spgemm(Mh, Mh))
+    res_p = markov_cluster(plan, Gd, iterations=3)
+    assert res_s.ip_history == res_p.ip_history
+    assert res_s.nnz_history == res_p.nnz_history
+    a, b = res_s.Mt.to_host(), res_p.Mt.to_host()
+    assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)
+    assert np.allclose(a.val, b.val, rtol=1e-4, atol=1e-7)

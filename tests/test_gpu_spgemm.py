@@ -9,6 +9,7 @@ import torch
 import oracle
 from paper_2512_12036_gb300 import DeviceCSR, Plan, SpgemmError, gen
 from paper_2512_12036_gb300 import _lib
+from contraction import assignment_labels, label_scatter
 from parity import compare
 
 pytestmark = pytest.mark.gpu
@@ -472,3 +473,30 @@ def test_malformed_input_reported_not_faulted(plan, what):
     C = plan.spgemm(DeviceCSR.from_host(gen.erdos_renyi(50, 3, seed=9)),
                     DeviceCSR.from_host(gen.erdos_renyi(50, 3, seed=9)))
     assert C.nnz > 0
+
+
+@pytest.mark.parametrize("scale,clusters", [(12, 256), (14, 1024)])
+def test_contraction_full_StAS(plan, scale, clusters):
+    """Both products of the contraction S^T*A*S (Algorithm 7) on an R-MAT
+    graph: each product against the oracle on the inputs it actually got
+    (exact structure, 1e-5 * sum|a||b|), and the final result against A's
+    entries scattered by cluster labels in fp64 (exact structure; values
+    within 2e-5 * sum|a|, one 1e-5 share per product)."""
+    A_h = gen.rmat_symmetric(scale, 16, 0.57, 0.19, 0.19, seed=2 + scale)
+    S_h = gen.assignment_matrix(A_h.rows, clusters, seed=3)
+    St_h = gen.transpose_structure(S_h)
+    A, S, St = DeviceCSR.from_host(A_h), DeviceCSR.from_host(S_h), DeviceCSR.from_host(St_h)
+    T = plan.spgemm(St, A)
+    C2 = plan.spgemm(T, S)
+    torch.cuda.synchronize()
+    T_h, C2_h = T.to_host(), C2.to_host()
+    compare(T_h, oracle.spgemm(St_h, A_h))
+    compare(C2_h, oracle.spgemm(T_h, S_h))
+    rp, col, val, absum = label_scatter(A_h, assignment_labels(S_h), clusters)
+    assert np.array_equal(C2_h.row_ptr.astype(np.int64), rp)
+    assert np.array_equal(C2_h.col, col)
+    err = np.abs(C2_h.val.astype(np.float64) - val)
+    assert (err <= 2e-5 * absum).all()
+    # the contraction preserves the total weight of the graph
+    assert abs(float(C2_h.val.astype(np.float64).sum()) - float(A_h.val.astype(np.float64).sum())) \
+        <= 2e-5 * float(np.abs(A_h.val.astype(np.float64)).sum())
