@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--gnn-graphs", type=int, default=8192)
     ap.add_argument("--panel-cols", type=int, default=None)
     ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--no-row-cache", action="store_true",
+                    help="accumulation phase without the allocation phase's row bitmaps")
     ap.add_argument("--row-stride", type=int, default=1,
                     help="left operand of A*A = every k-th row of A (a smaller case with the "
                          "same row mix and the full right operand, for profiling; not the "
@@ -665,6 +667,24 @@ def pattern_er4096(device, reps: int = 50):
             "oracle_ms": cpu_ms, "oracle_cores": host_threads(), "matches_oracle": ok}
 
 
+def row_cache_size(plan, L, A, device) -> int:
+    """MiB of row bitmap cache that holds every row of L*A that reaches a
+    dense accumulation tier (one B.cols-bit bitmap per row, plus the slot
+    index of every row), or as much of it as free device memory allows
+    beside the output (8 bytes per entry of C) and 16 GiB of headroom."""
+    import torch
+    ws = plan.workspace(L, A)
+    ip_row, _ = plan.count(L, A, ws)
+    row_nnz, nnz = plan.symbolic(L, A, ip_row, ws)
+    dense = int((row_nnz > plan.opts["block_max_nnz"]).sum().item())
+    del ws, ip_row, row_nnz
+    torch.cuda.empty_cache()
+    need = dense * ((A.cols + 31) // 32) * 4 + 4 * L.rows + (1 << 20)
+    free, _ = torch.cuda.mem_get_info(device)
+    room = free - 8 * nnz - (16 << 30)
+    return int(max(0, min(need, room)) >> 20)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -693,32 +713,40 @@ def run_ours(args):
     opts = {}
     if args.panel_cols:
         opts["panel_cols"] = args.panel_cols
-    plan = Plan(device=local, **opts)
+    # the contraction's products run on a plan without the row bitmap cache
+    plan_c = Plan(device=local, **opts)
+    cache_mb = 0 if args.no_row_cache else row_cache_size(plan_c, L, A, dev)
+    plan = Plan(device=local, row_cache_mb=cache_mb, **opts)
     ws_aa = plan.workspace(L, A)
-    ws_sa = plan.workspace(St, A)
+    ws_sa = plan_c.workspace(St, A)
 
     # first pass: sizes and output buffers (untimed)
     blocks, ip_aa, nnz_aa = plan.spgemm_blocks(L, A, ws=ws_aa)
-    T_blocks, ip_sa, _ = plan.spgemm_blocks(St, A, ws=ws_sa)
+    T_blocks, ip_sa, _ = plan_c.spgemm_blocks(St, A, ws=ws_sa)
     T = T_blocks[0][2]
-    ws_ts = plan.workspace(T, S)
-    C2_blocks, ip_ts, nnz_ts = plan.spgemm_blocks(T, S, ws=ws_ts)
-    for ws in (ws_aa, ws_sa, ws_ts):
-        plan.check_status(ws, "first pass")
+    ws_ts = plan_c.workspace(T, S)
+    C2_blocks, ip_ts, nnz_ts = plan_c.spgemm_blocks(T, S, ws=ws_ts)
+    plan.check_status(ws_aa, "first pass")
+    for ws in (ws_sa, ws_ts):
+        plan_c.check_status(ws, "first pass")
     ip_step = ip_aa + ip_sa + ip_ts
     n_blocks = len(blocks)
     stream = torch.cuda.current_stream()
 
     def step():
         plan.spgemm_blocks(L, A, ws=ws_aa, out=blocks)
-        plan.spgemm_blocks(St, A, ws=ws_sa, out=T_blocks)
-        plan.spgemm_blocks(T, S, ws=ws_ts, out=C2_blocks)
+        plan_c.spgemm_blocks(St, A, ws=ws_sa, out=T_blocks)
+        plan_c.spgemm_blocks(T, S, ws=ws_ts, out=C2_blocks)
+
+    def check_all(where):
+        plan.check_status(ws_aa, where)
+        for ws in (ws_sa, ws_ts):
+            plan_c.check_status(ws, where)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    for ws in (ws_aa, ws_sa, ws_ts):
-        plan.check_status(ws, "warm-up")
+    check_all("warm-up")
 
     def barrier():
         if world > 1:
@@ -727,7 +755,8 @@ def run_ours(args):
 
     # ---- timed region (device-resident inputs)
     plan.profile(True)
-    launches0 = plan.launches()
+    plan_c.profile(True)
+    launches0 = plan.launches() + plan_c.launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     with ClockSampler(local) as clk:
@@ -737,11 +766,14 @@ def run_ours(args):
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
-    launches = plan.launches() - launches0
+    launches = plan.launches() + plan_c.launches() - launches0
     prof = plan.profile_read()
+    for k, (t_ms, n) in plan_c.profile_read().items():
+        a_ms, a_n = prof.get(k, (0.0, 0))
+        prof[k] = (a_ms + t_ms, a_n + n)
     plan.profile(False)
-    for ws in (ws_aa, ws_sa, ws_ts):
-        plan.check_status(ws, "timed steps")
+    plan_c.profile(False)
+    check_all("timed steps")
     ms = max_over_ranks(ms, dev)
     ms_step = ms / args.steps
     value = 2.0 * ip_step * world / (ms_step / 1e3) / 1e9
@@ -751,6 +783,7 @@ def run_ours(args):
     ip_row, _ = plan.count(L, A, ws_aa, ip_row=ip_row)
     nnz_row, _ = plan.symbolic(L, A, ip_row, ws_aa)
     work = tier_work(plan, L_h, ip_row.cpu().numpy(), nnz_row.to(torch.int64).cpu().numpy())
+    rows_cached = plan.row_cache_rows(L, A, ws_aa)
     top = max(prof.items(), key=lambda kv: kv[1][0])
     top_name, (top_ms, top_n) = top
     peaks = {}
@@ -854,6 +887,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (fp64 accumulation where "
             "more than 167 terms can meet)", "data": "synthetic",
+            "row_cache": {"mib": cache_mb, "rows_with_slot": rows_cached},
             "config": {"workload": workload_name(args.scale, args.row_stride),
                        "rmat_scale": args.scale, "row_stride_AxA": args.row_stride,
                        "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05],

@@ -80,7 +80,15 @@ typedef struct {
     int32_t block_max_nnz;    /* default 8192: accumulation phase, block-per-row hash tier */
     int32_t panel_cols;       /* default 16384 (a power of two, 1024..16384): column panel of
                                  the dense heavy-row accumulator */
-    int32_t reserved[9];
+    int32_t row_cache_mb;     /* default 0: MiB of workspace for the allocation phase's
+                                 row bitmaps. The allocation phase's bitmap tier keeps the
+                                 column bitmap (B.cols bits) of every row that the
+                                 accumulation phase will take in a dense tier, one slot per
+                                 row while slots last; the accumulation phase then reads a
+                                 row's columns from its slot instead of marking every product
+                                 again. Rows without a slot are unaffected. B.cols must be at
+                                 most 1,572,864 for the cache to be used. */
+    int32_t reserved[8];
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;

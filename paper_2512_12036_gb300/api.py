@@ -130,6 +130,19 @@ class Plan:
         check(_lib.lib().spgemm_workspace_init(self.handle, _ptr(ws), ws.numel(), _stream(stream)),
               "spgemm_workspace_init")
 
+    def row_cache_rows(self, A: DeviceCSR, B: DeviceCSR, ws: torch.Tensor) -> int:
+        """Rows that hold a slot of the row bitmap cache after the last
+        allocation phase on this workspace (0 without a cache)."""
+        if self.opts.get("row_cache_mb", 0) <= 0:
+            return 0
+        wpr = (B.cols + 31) // 32
+        slot_bytes = (4 * A.rows + 255) // 256 * 256
+        nslots = min(A.rows, max(0, ((self.opts["row_cache_mb"] << 20) - slot_bytes) // (4 * wpr)))
+        if wpr == 0 or wpr > 48 * 1024:
+            nslots = 0
+        used = int(ws[:16].view(torch.int32)[2].item())     # slots asked for (control block)
+        return min(used, nslots)
+
     # ------------------------------------------------------------------ phases
     def count(self, A: DeviceCSR, B: DeviceCSR, ws: torch.Tensor, ip_row: torch.Tensor | None = None,
               total: bool = True, stream=None):

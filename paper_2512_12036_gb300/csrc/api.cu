@@ -42,6 +42,22 @@ WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long lon
         L.bhot = off;
         off = align256(off + sizeof(int) * (size_t)b_nnz);
     }
+    const long long wpr = (b_cols + 31) / 32;
+    if (p->opts.row_cache_mb > 0 && m > 0 && wpr > 0 && wpr <= kRowCacheMaxWords) {
+        const size_t bytes = (size_t)p->opts.row_cache_mb << 20;
+        const size_t slot_bytes = align256(sizeof(int) * (size_t)m);
+        const size_t row_bytes = sizeof(unsigned) * (size_t)wpr;
+        long long n = bytes > slot_bytes ? (long long)((bytes - slot_bytes) / row_bytes) : 0;
+        if (n > m) n = m;
+        if (n > 0) {
+            L.rc_nslots = (int)n;
+            L.rc_wpr = (int)wpr;
+            L.rc_slot = off;
+            off += slot_bytes;
+            L.rc_bits = off;
+            off = align256(off + row_bytes * (size_t)n);
+        }
+    }
     L.total = off;
     return L;
 }
@@ -59,6 +75,10 @@ WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols) {
     w.hot_rank = L.has_hot ? (int*)(b + L.hot_rank) : nullptr;
     w.hot_col = L.has_hot ? (int*)(b + L.hot_col) : nullptr;
     w.bhot = L.has_hot ? (int*)(b + L.bhot) : nullptr;
+    w.rc_slot = L.rc_nslots > 0 ? (int*)(b + L.rc_slot) : nullptr;
+    w.rc_bits = L.rc_nslots > 0 ? (unsigned*)(b + L.rc_bits) : nullptr;
+    w.rc_nslots = L.rc_nslots;
+    w.rc_wpr = L.rc_wpr;
     w.nblk = L.nblk;
     w.nscan = L.nscan;
     w.panels = L.panels;
@@ -221,6 +241,7 @@ int spgemm_plan_create(spgemm_plan** out, const spgemm_opts* opts, int device) {
     if (o.panel_cols < 1024 || o.panel_cols > 16384 || (o.panel_cols & (o.panel_cols - 1)))
         return SPGEMM_ERR_INVALID;
     if (o.fp32_max_terms < 0) return SPGEMM_ERR_INVALID;
+    if (o.row_cache_mb < 0) return SPGEMM_ERR_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return SPGEMM_ERR_CUDA;

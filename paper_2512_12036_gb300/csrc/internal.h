@@ -97,6 +97,9 @@ struct WsLayout {
     size_t hot_rank = 0;     // int32 [B.cols+1]  exclusive prefix of the hot flags
     size_t hot_col = 0;      // int32 [B.cols]    hot columns in ascending order
     size_t bhot = 0;         // int32 [B.nnz]     each B entry's column, or (sign bit | hot rank)
+    size_t rc_slot = 0;      // int32 [m]         row -> bitmap slot (-1: none)
+    size_t rc_bits = 0;      // u32 [rc_nslots][rc_wpr] row bitmaps of the allocation phase
+    int rc_nslots = 0, rc_wpr = 0;
     bool has_hot = false;
     size_t total = 0;
     int m = 0, nblk = 0, nscan = 0, panels = 0;
@@ -115,8 +118,15 @@ struct WsPtrs {
     int* hot_rank;
     int* hot_col;
     int* bhot;
+    int* rc_slot;            // nullptr: no row bitmap cache
+    unsigned* rc_bits;
+    int rc_nslots, rc_wpr;
     int nblk, nscan, panels, panel_cols;
 };
+
+// Row bitmap cache: rows of B.cols bits, written by the allocation phase's
+// bitmap tier for rows the accumulation phase takes in a dense tier.
+constexpr int kRowCacheMaxWords = 48 * 1024;   // one bitmap pass of the allocation tier
 
 WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols);
 

@@ -705,13 +705,18 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
 constexpr int kRankPanels = 24;       // 8 and 16 measured slower, 32 leaves too few values
 constexpr int kRankOccUnroll = 8;     // occupancy expansion items are one int
 
+// With a row bitmap cache, a row that holds a slot reads each pass's bitmap
+// words from it (one coalesced copy) instead of the occupancy expansion.
 __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, CsrDev B,
                                                                    const int* map, Ctl* ctl,
                                                                    const int* rptC, int row_begin,
                                                                    int* colC, float* valC,
                                                                    int bin_lo, int bin_hi, int tier,
                                                                    const int* tab, int P, int PW,
-                                                                   int pmax, int cap) {
+                                                                   int pmax, int cap,
+                                                                   const int* rc_slot,
+                                                                   const unsigned* rc_bits,
+                                                                   int rc_nslots, int rc_wpr) {
     constexpr int kT = kD32Threads;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int RW = (pmax * PW) >> 5;                  // words of the widest pass
@@ -747,8 +752,11 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
         }
         const int w = (int)(kk >> 5);
         if ((unsigned)(w - lo) >= (unsigned)(hi - lo)) return;            // other word range
-        const int r = rk[w] + __popc(bm[w] & ((1u << (kk & 31)) - 1u)) - rbase;
-        if ((unsigned)r < (unsigned)cap) atomicAdd(&vals[r], a * kv.v);
+        const unsigned word = bm[w];
+        const int r = rk[w] + __popc(word & ((1u << (kk & 31)) - 1u)) - rbase;
+        // the column must be in the pass's bitmap (a cached bitmap that does
+        // not match the operands is reported, not used)
+        if ((unsigned)r < (unsigned)cap && ((word >> (kk & 31)) & 1u)) atomicAdd(&vals[r], a * kv.v);
         else set_status(ctl, ST_INTERNAL);
     };
 
@@ -766,6 +774,12 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
         row_extent(A, row, rs, re, ctl);
         const int na = re - rs;
         if (na > kT) continue;                        // fallback kernel's row
+        int cslot = rc_slot != nullptr ? rc_slot[row] : -1;
+        if (cslot >= rc_nslots) {
+            set_status(ctl, ST_INTERNAL);
+            cslot = -1;
+        }
+        const unsigned* cbits = cslot >= 0 ? rc_bits + (size_t)cslot * rc_wpr : nullptr;
         const long long per_panel = ((long long)nnz_row + P - 1) / P;
         long long want = per_panel > 0 ? (3ll * cap / 4) / per_panel : pmax;
         const int ppp = (int)(want < 1 ? 1 : (want > pmax ? pmax : want));
@@ -802,10 +816,16 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                     len = nxt - cur;
                 }
             }
-            // 1. occupancy
-            expand_tile_padded<kT, float, kRankOccUnroll>(tile, bs, len, mya, load_key, mark);
-            // 2. word ranks and the pass's columns (thread t owns words [wb, wb + wpt))
+            // 1. occupancy (c0 is a multiple of the panel width, so of 32)
             const int nw = (span + 31) >> 5;
+            if (cbits != nullptr) {
+                const unsigned* src = cbits + (c0 >> 5);
+                for (int i = t; i < nw; i += kT) bm[i] = src[i];
+                __syncthreads();
+            } else {
+                expand_tile_padded<kT, float, kRankOccUnroll>(tile, bs, len, mya, load_key, mark);
+            }
+            // 2. word ranks and the pass's columns (thread t owns words [wb, wb + wpt))
             const int wpt = (nw + kT - 1) / kT;
             const int wb = t * wpt;
             int cnt = 0;
@@ -902,7 +922,10 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                                                                   const int* tab, int P, int PW,
                                                                   int ppp, const int* hot_rank,
                                                                   const int* hot_col,
-                                                                  const int* bhot) {
+                                                                  const int* bhot,
+                                                                  const int* rc_slot,
+                                                                  const unsigned* rc_bits,
+                                                                  int rc_nslots, int rc_wpr) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int W = PW * ppp;                                           // columns per pass
     double* acc = reinterpret_cast<double*>(sm_raw);                  // [kHotSlots]
@@ -930,6 +953,9 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
     // pass start, sub-pass columns [lo, hi), its hot ranks [hr0, hr0 + nhs),
     // and the pass's hot ranks [hrp0, hrp1)
     int pc0 = 0, lo = 0, hi = 0, hr0 = 0, nhs = 0, hrp0 = 0, hrp1 = 0;
+    // the row's cached column bitmap (allocation phase), or nullptr: with it
+    // the sub-pass's bitmap words are copied in and products mark nothing
+    const unsigned* cbits = nullptr;
     auto load = [&](int q) { return KeyVal{bhot[q], B.val[q]}; };
     // one bitmap OR and one fp32 add per product, hot or cold, on selected
     // addresses (a hot product marks its slot, a cold one its column), so the
@@ -955,7 +981,8 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
             }
             x = code - pc0;
         }
-        atomicOr((hot ? touched : bm) + (x >> 5), 1u << (x & 31));
+        if (cbits == nullptr) atomicOr((hot ? touched : bm) + (x >> 5), 1u << (x & 31));
+        else if (!hot && !((bm[x >> 5] >> (x & 31)) & 1u)) set_status(ctl, ST_INTERNAL);
         if (hot && !split) atomicAdd(&acc[x], (double)a * (double)kv.v);
         else atomicAdd(hot ? &cp[(seg & (kHotCopies - 1)) * kHotSlots + x] : &st[x], a * kv.v);
     };
@@ -987,6 +1014,14 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
         row_extent(A, row, rs, re, ctl);
         const int na = re - rs;
         const bool cached = use_tab && na <= kHotThreads;
+        {
+            int cslot = rc_slot != nullptr ? rc_slot[row] : -1;
+            if (cslot >= rc_nslots) {
+                set_status(ctl, ST_INTERNAL);
+                cslot = -1;
+            }
+            cbits = cslot >= 0 ? rc_bits + (size_t)cslot * rc_wpr : nullptr;
+        }
         int myk = -1, cur = 0, nxt = 0;
         float mya = 0.f;
         if (cached && t < na) {
@@ -1033,6 +1068,18 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                     set_status(ctl, ST_INTERNAL);
                     nhs = nhs < 0 ? 0 : kHotSlots;
                 }
+                if (cbits != nullptr) {
+                    // the sub-pass's columns [lo, hi) of the cached bitmap (words
+                    // outside it stay clear); the expansion's block scan orders
+                    // these stores before any product reads them
+                    const int w0 = (lo - pc0) >> 5, w1 = (hi - pc0 + 31) >> 5;
+                    for (int q = w0 + t; q < w1; q += kHotThreads) {
+                        unsigned v = cbits[(pc0 >> 5) + q];
+                        if (q == w0) v &= ~0u << ((lo - pc0) & 31);
+                        if (q == w1 - 1 && ((hi - pc0) & 31)) v &= (1u << ((hi - pc0) & 31)) - 1u;
+                        bm[q] = v;
+                    }
+                }
                 if (cached) {
                     // packed expansion: this tier's per-pass segments are often short
                     expand_tile<kHotThreads, float, kHotUnroll, true>(tile, bs, len, mya, load,
@@ -1069,7 +1116,8 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                     const int kk = hot_col[hr0 + h] - pc0;
                     if ((unsigned)kk < (unsigned)W) {
                         st[kk] = (float)acc[h];
-                        if ((touched[h >> 5] >> (h & 31)) & 1u) atomicOr(&bm[kk >> 5], 1u << (kk & 31));
+                        if (cbits == nullptr && ((touched[h >> 5] >> (h & 31)) & 1u))
+                            atomicOr(&bm[kk >> 5], 1u << (kk & 31));
                     }
                     acc[h] = 0.0;
                 }
@@ -1264,7 +1312,8 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
         SPG_LAUNCH(p, K_NUM_DENSE32, s,
                    k_num_dense_rank<<<sms * p->occ_num_rank, kD32Threads, rank_smem(p, pmax, PW), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
-                       NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW, pmax, cap));
+                       NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW, pmax, cap,
+                       w.rc_slot, w.rc_bits, w.rc_nslots, w.rc_wpr));
         SPG_LAUNCH(p, K_NUM_DENSE32, s,
                    k_num_dense<0, kD32Threads><<<sms * p->occ_num_dense32, kD32Threads, num_dense_smem(p, 0), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
@@ -1280,7 +1329,8 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                    k_num_dense_hot<<<sms * p->occ_num_dense_hot, kHotThreads, num_dense_hot_smem(p), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
                        NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW, p->hot_ppp,
-                       w.hot_rank, w.hot_col, w.bhot));
+                       w.hot_rank, w.hot_col, w.bhot, w.rc_slot, w.rc_bits, w.rc_nslots,
+                       w.rc_wpr));
         return;
     }
     SPG_LAUNCH(p, K_NUM_DENSE64, s,

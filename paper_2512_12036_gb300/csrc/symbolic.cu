@@ -151,13 +151,19 @@ __global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev
 }
 
 // ---------------------------------------------------------------------------
+// With a row bitmap cache (rc_slot != nullptr), a row that fits one pass and
+// whose entry count puts it in a dense accumulation tier (nnz > cache_min)
+// takes the next free slot and leaves its column bitmap there for the
+// accumulation phase.
 __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, CsrDev B,
                                                                 const int* map, Ctl* ctl,
                                                                 int* row_nnz, int bin_lo,
                                                                 int bin_hi, int tier,
-                                                                int nwords) {
+                                                                int nwords, int* rc_slot,
+                                                                unsigned* rc_bits, int rc_nslots,
+                                                                int rc_wpr, int cache_min) {
     extern __shared__ unsigned bm[];
-    __shared__ int s_idx;
+    __shared__ int s_idx, s_slot;
     __shared__ int red[33];
     __shared__ ExpandTile<kSymDenseThreads, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
@@ -192,9 +198,32 @@ __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, Csr
             int cnt = 0;
             for (int q = threadIdx.x; q < nw; q += blockDim.x) cnt += __popc(bm[q]);
             nnz += block_sum(cnt, red);
+            // (block_sum ends with a barrier: bm is final here)
+            if (rc_slot != nullptr && c0l == 0 && B.cols <= span_max && nnz > cache_min &&
+                nw == rc_wpr) {
+                if (threadIdx.x == 0) {
+                    const int slot = atomicAdd(&ctl->rc_used, 1);
+                    s_slot = slot < rc_nslots ? slot : -1;
+                    rc_slot[row] = s_slot;
+                }
+                __syncthreads();
+                const int slot = s_slot;
+                if (slot >= 0) {
+                    unsigned* dst = rc_bits + (size_t)slot * rc_wpr;
+                    for (int q = threadIdx.x; q < nw; q += blockDim.x) dst[q] = bm[q];
+                }
+            }
         }
         if (threadIdx.x == 0) row_nnz[row] = nnz;
     }
+}
+
+// Every row starts without a cached bitmap; the slot counter restarts.
+__global__ void k_rc_reset(int* rc_slot, int m, Ctl* ctl) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x)
+        rc_slot[i] = -1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rc_used = 0;
 }
 
 // Narrow B (<= kNarrowCols columns): one warp per row marks the row's
@@ -271,6 +300,8 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     launch_group(p, g, w, w.map, nullptr, s);
     if (A.rows == 0) return;
     const int sms = p->num_sms;
+    if (w.rc_slot)
+        SPG_LAUNCH(p, K_FILL, s, k_rc_reset<<<sms * 4, 256, 0, s>>>(w.rc_slot, A.rows, w.ctl));
     SPG_LAUNCH(p, K_SYM_ESC, s, k_sym_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, row_nnz, SB_ESC));
     const size_t sw = (size_t)kWarpsPerBlockSW * kWarpTableSym * 4;
     SPG_LAUNCH(p, K_SYM_WARP, s,
@@ -289,7 +320,8 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     const size_t sd = sym_dense_smem(p);
     SPG_LAUNCH(p, K_SYM_DENSE, s,
                k_sym_dense<<<sms * p->occ_sym_dense, kSymDenseThreads, sd, s>>>(
-                   A, B, w.map, w.ctl, row_nnz, SB_DENSE0, SB_DENSE0 + SB_DENSE_N, 1, (int)(sd / 4)));
+                   A, B, w.map, w.ctl, row_nnz, SB_DENSE0, SB_DENSE0 + SB_DENSE_N, 1, (int)(sd / 4),
+                   w.rc_slot, w.rc_bits, w.rc_nslots, w.rc_wpr, p->opts.block_max_nnz));
 }
 
 }  // namespace spg

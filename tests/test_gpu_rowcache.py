@@ -1,0 +1,84 @@
+"""The allocation phase's row bitmap cache (opts.row_cache_mb): products whose
+dense rows read their columns from the cache match the oracle exactly as
+without it, in both dense accumulation tiers (fp32 rank-compacted and the
+fp64-bound tier with hot-column partial sums), with every dense row cached,
+with only some rows cached (the rest recompute their occupancy), across
+row blocks of the accumulation phase, and after a second allocation phase
+on the same workspace (slots restart). A cache that no longer matches B is
+reported on the status word."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2512_12036_gb300 import DeviceCSR, Plan, SpgemmError, gen
+from parity import compare
+from test_gpu_spgemm import hub_matrix
+
+pytestmark = pytest.mark.gpu
+
+
+def operands():
+    B = hub_matrix(3000, 70000, 15, heavy_rows=set(range(0, 3000, 11)), heavy_len=200,
+                   light_deg=20)
+    # dense rows with few A entries (fp32 tier), with > 167 (fp64 tier), with
+    # more than one tile (> 1024 entries, uncached-tile path)
+    A = hub_matrix(300, 3000, 16, heavy_rows=set(range(0, 300, 9)) | {1, 2}, heavy_len=2500,
+                   light_deg=150)
+    return A, B
+
+
+def dense_rows(A, B, plan):
+    nnz = oracle.symbolic(A, B)
+    return int((nnz > plan.opts["block_max_nnz"]).sum()), nnz
+
+
+@pytest.mark.parametrize("cache_mb", [64, 1])
+def test_row_cache_parity(cache_mb):
+    A, B = operands()
+    plan = Plan(row_cache_mb=cache_mb)
+    ndense, nnz = dense_rows(A, B, plan)
+    na = np.diff(A.row_ptr)
+    assert ndense > 20 and (na[nnz > 8192] <= 167).any() and (na[nnz > 8192] > 1024).any()
+    dA, dB = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
+    ws = plan.workspace(dA, dB)
+    for rep in range(2):                      # a second allocation phase reuses the slots
+        blocks, _, _ = plan.spgemm_blocks(dA, dB, ws=ws, max_block_nnz=int(nnz.sum()) // 3 + 1)
+        torch.cuda.synchronize()
+        plan.check_status(ws, "row cache")
+        assert len(blocks) >= 3
+        cached = plan.row_cache_rows(dA, dB, ws)
+        slots_fit = (cache_mb << 20) // (4 * ((B.cols + 31) // 32))
+        assert cached == min(ndense, slots_fit - 1) or cached == min(ndense, slots_fit)
+        if cache_mb == 1:
+            assert 0 < cached < ndense          # some rows cached, some not
+        rows = np.concatenate([np.diff(Cb.row_ptr.cpu().numpy()) for _, _, Cb in blocks])
+        assert np.array_equal(rows, nnz)
+        for r0, r1, Cb in blocks:
+            compare(Cb.to_host(), oracle.spgemm(A, B, rows=np.arange(r0, r1)))
+
+
+def test_row_cache_mismatch_reported():
+    """Accumulation with a B whose columns differ from the allocation phase's:
+    the cached bitmaps no longer match and the status word says so."""
+    A, B = operands()
+    rng = np.random.default_rng(3)
+    B2 = gen.HostCSR(B.rows, B.cols, B.row_ptr.copy(),
+                     np.sort(rng.integers(0, B.cols, size=B.nnz).astype(np.int32)),
+                     B.val.copy())
+    # keep every row sorted (the panel table of B stays usable)
+    for i in range(B2.rows):
+        s, e = B2.row_ptr[i], B2.row_ptr[i + 1]
+        B2.col[s:e] = np.sort(rng.choice(B.cols, size=e - s, replace=False))
+    plan = Plan(row_cache_mb=64)
+    dA, dB, dB2 = DeviceCSR.from_host(A), DeviceCSR.from_host(B), DeviceCSR.from_host(B2)
+    ws = plan.workspace(dA, dB)
+    ip_row, _ = plan.count(dA, dB, ws)
+    row_nnz, nnz = plan.symbolic(dA, dB, ip_row, ws)
+    rp, _ = plan.row_ptr(row_nnz, ws)
+    col = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    val = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    plan.numeric(dA, dB2, ip_row, rp, ws, col, val)
+    torch.cuda.synchronize()
+    with pytest.raises(SpgemmError):
+        plan.check_status(ws, "stale row cache")
