@@ -18,13 +18,27 @@ from test_gpu_spgemm import hub_matrix
 pytestmark = pytest.mark.gpu
 
 
-def operands():
-    B = hub_matrix(3000, 70000, 15, heavy_rows=set(range(0, 3000, 11)), heavy_len=200,
+def operands(bcols=70000):
+    B = hub_matrix(3000, bcols, 15, heavy_rows=set(range(0, 3000, 11)), heavy_len=200,
                    light_deg=20)
-    # dense rows with few A entries (fp32 tier), with > 167 (fp64 tier), with
-    # more than one tile (> 1024 entries, uncached-tile path)
-    A = hub_matrix(300, 3000, 16, heavy_rows=set(range(0, 300, 9)) | {1, 2}, heavy_len=2500,
-                   light_deg=150)
+    # dense rows with few A entries (fp32 tier: 150 entries on heavy rows of
+    # B), with > 167 (fp64 tier: 400 entries), with more than one tile
+    # (2500 entries, uncached-tile path), and light rows
+    A = hub_matrix(300, 3000, 16, heavy_rows={1, 2, 100, 299}, heavy_len=2500, light_deg=30)
+    rng = np.random.default_rng(17)
+    heavy_b = np.arange(0, 3000, 11)
+    r = [np.repeat(np.arange(A.rows), np.diff(A.row_ptr))]
+    c = [A.col.astype(np.int64)]
+    for i, n in [(i, 150) for i in range(10, 300, 13)] + [(i, 400) for i in range(5, 300, 29)]:
+        if i in (1, 2, 100, 299):
+            continue
+        r.append(np.full(n, i))
+        c.append(rng.choice(heavy_b, size=n, replace=False) if n <= heavy_b.size
+                 else rng.choice(3000, size=n, replace=False))
+    r, c = np.concatenate(r), np.concatenate(c)
+    key = np.unique(r * 3000 + c)
+    r, c = key // 3000, key % 3000
+    A = gen.csr_from_coo(300, 3000, r, c, gen.uniform_open_closed(rng, r.size))
     return A, B
 
 
@@ -33,9 +47,9 @@ def dense_rows(A, B, plan):
     return int((nnz > plan.opts["block_max_nnz"]).sum()), nnz
 
 
-@pytest.mark.parametrize("cache_mb", [64, 1])
-def test_row_cache_parity(cache_mb):
-    A, B = operands()
+@pytest.mark.parametrize("bcols,cache_mb", [(70000, 64), (1_000_000, 1)])
+def test_row_cache_parity(bcols, cache_mb):
+    A, B = operands(bcols)
     plan = Plan(row_cache_mb=cache_mb)
     ndense, nnz = dense_rows(A, B, plan)
     na = np.diff(A.row_ptr)
@@ -50,8 +64,10 @@ def test_row_cache_parity(cache_mb):
         cached = plan.row_cache_rows(dA, dB, ws)
         slots_fit = (cache_mb << 20) // (4 * ((B.cols + 31) // 32))
         assert cached == min(ndense, slots_fit - 1) or cached == min(ndense, slots_fit)
-        if cache_mb == 1:
+        if bcols > 100000:
             assert 0 < cached < ndense          # some rows cached, some not
+        else:
+            assert cached == ndense
         rows = np.concatenate([np.diff(Cb.row_ptr.cpu().numpy()) for _, _, Cb in blocks])
         assert np.array_equal(rows, nnz)
         for r0, r1, Cb in blocks:
