@@ -43,17 +43,22 @@ def operands(bcols=70000):
 
 
 def dense_rows(A, B, plan):
+    """(rows of C in a dense accumulation tier, rows of those that the
+    allocation phase's bitmap tier handles (IP above the block tier), nnz)."""
     nnz = oracle.symbolic(A, B)
-    return int((nnz > plan.opts["block_max_nnz"]).sum()), nnz
+    ip, _ = oracle.ip_count(A, B)
+    dense = nnz > plan.opts["block_max_nnz"]
+    return int(dense.sum()), int((dense & (ip > plan.opts["block_max_ip"])).sum()), nnz
 
 
 @pytest.mark.parametrize("bcols,cache_mb", [(70000, 64), (1_000_000, 1)])
 def test_row_cache_parity(bcols, cache_mb):
     A, B = operands(bcols)
     plan = Plan(row_cache_mb=cache_mb)
-    ndense, nnz = dense_rows(A, B, plan)
+    ndense, nbitmap, nnz = dense_rows(A, B, plan)
     na = np.diff(A.row_ptr)
     assert ndense > 20 and (na[nnz > 8192] <= 167).any() and (na[nnz > 8192] > 1024).any()
+    assert 0 < nbitmap < ndense        # dense rows with and without a bitmap from the allocation phase
     dA, dB = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
     ws = plan.workspace(dA, dB)
     for rep in range(2):                      # a second allocation phase reuses the slots
@@ -63,11 +68,11 @@ def test_row_cache_parity(bcols, cache_mb):
         assert len(blocks) >= 3
         cached = plan.row_cache_rows(dA, dB, ws)
         slots_fit = (cache_mb << 20) // (4 * ((B.cols + 31) // 32))
-        assert cached == min(ndense, slots_fit - 1) or cached == min(ndense, slots_fit)
+        assert cached == min(nbitmap, slots_fit - 1) or cached == min(nbitmap, slots_fit)
         if bcols > 100000:
-            assert 0 < cached < ndense          # some rows cached, some not
+            assert 0 < cached < nbitmap         # the slots ran out
         else:
-            assert cached == ndense
+            assert cached == nbitmap
         rows = np.concatenate([np.diff(Cb.row_ptr.cpu().numpy()) for _, _, Cb in blocks])
         assert np.array_equal(rows, nnz)
         for r0, r1, Cb in blocks:
