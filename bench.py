@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--gnn-graphs", type=int, default=8192)
     ap.add_argument("--panel-cols", type=int, default=None)
     ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--dense-splits", type=int, default=None,
+                    help="work items per heavy row in the fp64-bound dense tier")
     ap.add_argument("--no-row-cache", action="store_true",
                     help="accumulation phase without the allocation phase's row bitmaps")
     ap.add_argument("--row-stride", type=int, default=1,
@@ -716,6 +718,8 @@ def run_ours(args):
     # the contraction's products run on a plan without the row bitmap cache
     plan_c = Plan(device=local, **opts)
     cache_mb = 0 if args.no_row_cache else row_cache_size(plan_c, L, A, dev)
+    if args.dense_splits:
+        opts["dense_splits"] = args.dense_splits
     plan = Plan(device=local, row_cache_mb=cache_mb, **opts)
     ws_aa = plan.workspace(L, A)
     ws_sa = plan_c.workspace(St, A)

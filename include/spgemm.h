@@ -88,7 +88,12 @@ typedef struct {
                                  row's columns from its slot instead of marking every product
                                  again. Rows without a slot are unaffected. B.cols must be at
                                  most 1,572,864 for the cache to be used. */
-    int32_t reserved[8];
+    int32_t dense_splits;     /* default 0 (= 1): work items per heavy row in the fp64-bound
+                                 dense tier for rows with a cached bitmap. Each item takes one
+                                 of that many consecutive column ranges of the row, so one row
+                                 runs on up to that many SMs at once; items write disjoint,
+                                 ordered slices of the row (no merge step). */
+    int32_t reserved[7];
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;

@@ -43,6 +43,7 @@ struct spgemm_plan {
     int d32_ppp;           // and of the fp32 dense tier
     size_t rank_budget;    // dynamic shared memory of the rank-compacted fp32 dense kernel
     int occ_num_rank;
+    int hotr_cap, hotr_pmax;   // rank-compacted fp64 dense kernel: value slots, panels per pass
 };
 
 namespace spg {

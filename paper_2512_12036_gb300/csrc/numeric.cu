@@ -925,7 +925,8 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                                                                   const int* bhot,
                                                                   const int* rc_slot,
                                                                   const unsigned* rc_bits,
-                                                                  int rc_nslots, int rc_wpr) {
+                                                                  int rc_nslots, int rc_wpr,
+                                                                  int skip_cached) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int W = PW * ppp;                                           // columns per pass
     double* acc = reinterpret_cast<double*>(sm_raw);                  // [kHotSlots]
@@ -982,7 +983,6 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
             x = code - pc0;
         }
         if (cbits == nullptr) atomicOr((hot ? touched : bm) + (x >> 5), 1u << (x & 31));
-        else if (!hot && !((bm[x >> 5] >> (x & 31)) & 1u)) set_status(ctl, ST_INTERNAL);
         if (hot && !split) atomicAdd(&acc[x], (double)a * (double)kv.v);
         else atomicAdd(hot ? &cp[(seg & (kHotCopies - 1)) * kHotSlots + x] : &st[x], a * kv.v);
     };
@@ -1020,6 +1020,7 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                 set_status(ctl, ST_INTERNAL);
                 cslot = -1;
             }
+            if (skip_cached && cslot >= 0) continue;          // k_num_dense_hotr's row
             cbits = cslot >= 0 ? rc_bits + (size_t)cslot * rc_wpr : nullptr;
         }
         int myk = -1, cur = 0, nxt = 0;
@@ -1140,6 +1141,282 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
     }
 }
 
+// fp64-bound dense tier with rank-compacted passes, for rows whose column
+// bitmap the allocation phase cached (rows without a slot stay with
+// k_num_dense_hot). With the row's columns known, a pass no longer needs a
+// dense value array over its columns: each bitmap word gets the rank of its
+// first entry, every product of a cold column adds into a compact value
+// array at its entry's rank (word rank + popcount of the lower bits), and a
+// pass is as wide as its entries allow (up to `cap` entries and
+// kHotrSlots hot columns; ~4 table panels on R-MAT hub rows instead of 2),
+// so a row takes about half as many passes, each with longer B segments.
+// Hot columns keep the partial-sum scheme of k_num_dense_hot (kHotCopies
+// fp32 copies by the product's A-entry rank, folded into fp64 after every
+// tile, rounded once), with kHotrSlots slots and the copies padded apart in
+// shared memory. A pass with more hot columns than slots (only where hot
+// columns cluster inside one panel) is walked once per slot range, cold
+// products being added in the first walk only.
+//
+// Work items are (row, split): the row's table panels are cut into `splits`
+// consecutive column ranges, each taken by whichever block draws it, so one
+// heavy row runs on several SMs at once. A range writes its columns and
+// values at the row's output offset plus the entries of the earlier ranges
+// (popcounts of the cached bitmap), so the pieces need no merge step: they
+// are column-disjoint and already in order.
+constexpr int kHotrSlots = 2048;
+constexpr int kHotrStride = kHotrSlots + 1;   // copies of one slot in different banks
+constexpr int kHotrUnroll = 4;
+
+__global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hotr(
+    CsrDev A, CsrDev B, const int* map, Ctl* ctl, const int* rptC, int row_begin, int* colC,
+    float* valC, int bin_lo, int bin_hi, int tier, const int* tab, int P, int PW, int pmax,
+    int cap, const int* hot_rank, const int* hot_col, const int* bhot, const int* rc_slot,
+    const unsigned* rc_bits, int rc_nslots, int rc_wpr, int splits) {
+    constexpr int kT = kHotThreads;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double* acc = reinterpret_cast<double*>(sm_raw);                  // [kHotrSlots]
+    float* cp = reinterpret_cast<float*>(acc + kHotrSlots);           // [kHotCopies][kHotrStride]
+    float* vals = cp + kHotCopies * kHotrStride;                      // [cap]
+    unsigned* bm = reinterpret_cast<unsigned*>(vals + cap);           // [pmax * PW / 32]
+    int* rk = reinterpret_cast<int*>(bm + ((pmax * PW) >> 5));        // [pmax * PW / 32]
+    __shared__ int s_item, s_p1;
+    __shared__ int scratch[33];
+    __shared__ int s_pc[kMaxPanels];    // entries of the item's panels
+    __shared__ int s_ph[kMaxPanels];    // hot columns of the item's panels
+    __shared__ ExpandTile<kT, float> tile;
+    const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
+    if (begin >= end) return;
+    if (tab == nullptr || (ctl->b_unsorted & 1) != 0 || rc_slot == nullptr) return;
+    const int t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    for (int i = t; i < kHotrSlots; i += kT) acc[i] = 0.0;
+    for (int i = t; i < kHotCopies * kHotrStride; i += kT) cp[i] = 0.f;
+    for (int i = t; i < cap; i += kT) vals[i] = 0.f;
+    const bool split = ctl->b_unsorted == 0;       // copies bound the terms per column
+    const long long stride = P + 1;
+    const int wpp = PW >> 5;                       // bitmap words per table panel
+
+    // pass start c0 and width span, hot ranks of this walk [hr0, hr0 + nhs),
+    // of the pass [hrp0, hrp1); cold: this walk adds cold products
+    int c0 = 0, span = 0, hr0 = 0, nhs = 0, hrp0 = 0, hrp1 = 0;
+    bool cold = true;
+    auto load = [&](int q) { return KeyVal{bhot[q], B.val[q]}; };
+    // one instruction sequence for hot and cold products: both compute a
+    // cold rank (a hot one on word 0) and add once at a selected address
+    auto apply = [&](KeyVal kv, float a, int seg) {
+        const int code = kv.key;
+        const bool hot = code < 0;                             // (sign bit | hot rank)
+        const int x = hot ? (code & 0x7fffffff) - hr0 : code - c0;
+        const bool ok = hot ? (unsigned)x < (unsigned)nhs : (cold && (unsigned)x < (unsigned)span);
+        const unsigned kk = (!hot && ok) ? (unsigned)x : 0u;
+        const unsigned word = bm[kk >> 5];
+        const int r = rk[kk >> 5] + __popc(word & ((1u << (kk & 31)) - 1u));
+        if (ok) {
+            if (!hot && (!((word >> (kk & 31)) & 1u) || (unsigned)r >= (unsigned)cap))
+                set_status(ctl, ST_INTERNAL);                                  // not in C's row
+            else if (hot && !split) atomicAdd(&acc[x], (double)a * (double)kv.v);
+            else atomicAdd(hot ? &cp[(seg & (kHotCopies - 1)) * kHotrStride + x] : &vals[r], a * kv.v);
+        } else if (hot) {
+            const int rank = code & 0x7fffffff;
+            if (rank < hrp0 || rank >= hrp1) set_status(ctl, ST_INTERNAL);    // outside the pass
+        } else if (cold && key_in(code, B, ctl)) {
+            set_status(ctl, ST_INTERNAL);                                      // outside the pass
+        }
+    };
+    auto fold = [&]() {
+        if (split) {
+            for (int h = t; h < nhs; h += kT) {
+                double v = acc[h];
+#pragma unroll
+                for (int c = 0; c < kHotCopies; ++c) {
+                    v += (double)cp[c * kHotrStride + h];
+                    cp[c * kHotrStride + h] = 0.f;
+                }
+                acc[h] = v;
+            }
+        }
+        __syncthreads();
+    };
+
+    for (;;) {
+        if (t == 0) s_item = atomicAdd(&ctl->work[tier], 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        const long long idx = begin + (long long)item / splits;
+        const int g = item % splits;
+        if (idx >= end) break;
+        const int r = map[idx];
+        const int row = row_begin + r;
+        const int out = rptC[r];
+        const int nnz_row = rptC[r + 1] - out;
+        const int cslot = rc_slot[row];
+        if (cslot < 0 || cslot >= rc_nslots) continue;     // k_num_dense_hot's row
+        const unsigned* cbits = rc_bits + (size_t)cslot * rc_wpr;
+        const int gp0 = (int)((long long)P * g / splits), gp1 = (int)((long long)P * (g + 1) / splits);
+        if (gp0 >= gp1) continue;
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        const int na = re - rs;
+        const bool cached = na <= kT;
+        // entries per panel (popcounts of the cached bitmap) and hot columns
+        // per panel for this item's panels; entries before them = its offset
+        int before = 0;
+        for (int p = warp; p < gp1; p += kT / 32) {
+            const int w0 = p * wpp, w1 = w0 + wpp < rc_wpr ? w0 + wpp : rc_wpr;
+            int c = 0;
+            for (int q = w0 + lane; q < w1; q += 32) c += __popc(cbits[q]);
+            c = warp_sum(c);
+            if (p >= gp0) {
+                if (lane == 0) {
+                    const long long cA = (long long)p * PW;
+                    const long long cB = cA + PW < B.cols ? cA + PW : B.cols;
+                    s_pc[p - gp0] = c;
+                    s_ph[p - gp0] = hot_rank[cB] - hot_rank[cA];
+                }
+            } else {
+                before += c;
+            }
+        }
+        int pass_base = block_sum(lane == 0 ? before : 0, scratch);   // (barrier: s_pc, s_ph ready)
+        int myk = -1, cur = 0;
+        float mya = 0.f;
+        if (cached && t < na) {
+            const int j = rs + t;
+            const int k = A.col[j];
+            if ((unsigned)k < (unsigned)B.rows) {
+                myk = k;
+                mya = A.val[j];
+                cur = tab[(long long)k * stride + gp0];
+            } else {
+                set_status(ctl, ST_INVALID);
+            }
+        }
+        const int item_base = pass_base;
+        for (int p0 = gp0; p0 < gp1;) {
+            if (t == 0) {                    // widest pass within cap entries and the hot slots
+                int p1 = p0, ent = 0, hot = 0;
+                while (p1 < gp1 && p1 - p0 < pmax) {
+                    const int c = s_pc[p1 - gp0], h = s_ph[p1 - gp0];
+                    if (p1 > p0 && (ent + c > cap || hot + h > kHotrSlots)) break;
+                    ent += c;
+                    hot += h;
+                    ++p1;
+                }
+                s_p1 = p1;
+            }
+            __syncthreads();
+            const int p1 = s_p1;
+            c0 = p0 * PW;
+            span = (int)((long long)p1 * PW < B.cols ? (long long)p1 * PW - c0 : B.cols - (long long)c0);
+            const int nw = (span + 31) >> 5;
+            int bs = 0, len = 0;
+            if (myk >= 0) {
+                const int nxt = tab[(long long)myk * stride + p1];
+                if (cur < 0 || nxt < cur || (long long)nxt > B.nnz) set_status(ctl, ST_INTERNAL);
+                else {
+                    bs = cur;
+                    len = nxt - cur;
+                }
+                cur = nxt;
+            }
+            // the pass's bitmap words, their ranks and the pass's columns
+            // (thread t owns words [wb, wb + wpt))
+            const unsigned* src = cbits + (c0 >> 5);
+            const int wpt = (nw + kT - 1) / kT;
+            const int wb = t * wpt;
+            int cnt = 0;
+            for (int q = 0; q < wpt; ++q)
+                if (wb + q < nw) {
+                    const unsigned v = src[wb + q];
+                    bm[wb + q] = v;
+                    cnt += __popc(v);
+                }
+            int tot;
+            int run = block_excl_scan(cnt, scratch, &tot);
+            if (tot > cap) set_status(ctl, ST_INTERNAL);          // cannot happen: cap >= panel width
+            for (int q = 0; q < wpt; ++q) {
+                const int w = wb + q;
+                if (w >= nw) break;
+                rk[w] = run;
+                unsigned bits = bm[w];
+                while (bits) {
+                    const int o = pass_base + run;
+                    if (o < nnz_row) colC[out + o] = c0 + w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    ++run;
+                }
+            }
+            // (the expansion's block scan orders bm / rk before any product)
+            hrp0 = hot_rank[c0];
+            hrp1 = hot_rank[c0 + span];
+            for (int sub = 0, h0 = hrp0; sub == 0 || h0 < hrp1; ++sub, h0 += nhs) {
+                hr0 = h0;
+                nhs = hrp1 - h0 < kHotrSlots ? hrp1 - h0 : kHotrSlots;
+                cold = sub == 0;
+                if (cached) {
+                    expand_tile<kT, float, kHotrUnroll, true>(tile, bs, len, mya, load, apply);
+                    fold();
+                } else {
+                    for (int tb = rs; tb < re; tb += kT) {
+                        const int j = tb + t;
+                        int tbs = 0, tlen = 0;
+                        float a = 0.f;
+                        if (j < re) {
+                            a_entry(A, B, j, tbs, tlen, ctl);
+                            a = A.val[j];
+                            if (tlen > 0) {
+                                const int* tk = tab + (long long)A.col[j] * stride;
+                                const int ps = tk[p0], pe = tk[p1];
+                                if (ps >= tbs && pe >= ps && pe <= tbs + tlen) {
+                                    tbs = ps;
+                                    tlen = pe - ps;
+                                } else {
+                                    set_status(ctl, ST_INTERNAL);
+                                    tlen = 0;
+                                }
+                            }
+                        }
+                        expand_tile<kT, float, kHotrUnroll, true>(tile, tbs, tlen, a, load, apply);
+                        fold();
+                    }
+                }
+                // round the slot range's sums once into the value array
+                for (int h = t; h < nhs; h += kT) {
+                    const int kk = hot_col[hr0 + h] - c0;
+                    const double v = acc[h];
+                    acc[h] = 0.0;
+                    if ((unsigned)kk < (unsigned)span) {
+                        const unsigned word = bm[kk >> 5];
+                        const int rr = rk[kk >> 5] + __popc(word & ((1u << (kk & 31)) - 1u));
+                        if (((word >> (kk & 31)) & 1u) && (unsigned)rr < (unsigned)cap)
+                            vals[rr] = (float)v;
+                        else if (v != 0.0)
+                            set_status(ctl, ST_INTERNAL);
+                    } else {
+                        set_status(ctl, ST_INTERNAL);
+                    }
+                }
+                __syncthreads();
+            }
+            for (int i = t; i < tot && i < cap; i += kT) {
+                const int o = pass_base + i;
+                if (o < nnz_row) valC[out + o] = vals[i];
+                vals[i] = 0.f;
+            }
+            __syncthreads();
+            pass_base += tot;
+            p0 = p1;
+        }
+        if (t == 0) {
+            int want = 0;
+            for (int p = gp0; p < gp1; ++p) want += s_pc[p - gp0];
+            if (pass_base - item_base != want || (splits == 1 && pass_base != nnz_row))
+                set_status(ctl, ST_INTERNAL);
+        }
+        __syncthreads();
+    }
+}
+
 // shared memory of the fp64 tier for ppp panels of pw columns per pass
 constexpr size_t hot_smem_of(int pw, int ppp) {
     return (sizeof(double) + sizeof(float) * kHotCopies) * kHotSlots + 4 * (size_t)pw * ppp +
@@ -1166,6 +1443,15 @@ static size_t rank_smem(const spgemm_plan* p, int pmax, int pw) {
 
 static size_t num_dense_hot_smem(const spgemm_plan* p) {
     return hot_smem_of(p->opts.panel_cols, p->hot_ppp);
+}
+
+// rank-compacted fp64 tier: hot slots and copies, a value array of `cap`
+// entries (at least one panel), bitmap words and word ranks of pmax panels
+static size_t hotr_fixed() {
+    return sizeof(double) * kHotrSlots + sizeof(float) * kHotCopies * kHotrStride;
+}
+static size_t hotr_smem(int pw, int pmax, int cap) {
+    return hotr_fixed() + 4 * (size_t)cap + (size_t)pmax * (pw / 32) * 8;
 }
 
 // kMode 0: fp32 values and a bitmap over three table panels; kMode 1: fp64
@@ -1207,6 +1493,20 @@ void occupancy_numeric(spgemm_plan* p) {
         cudaFuncAttributes fa{};
         cudaFuncGetAttributes(&fa, (const void*)k_num_dense_rank);
         p->rank_budget = p->smem_optin > fa.sharedSizeBytes ? p->smem_optin - fa.sharedSizeBytes : 0;
+    }
+    // rank-compacted fp64 tier: 20480 value slots (at least one panel), as
+    // many panels per pass as the rest of shared memory holds
+    {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, (const void*)k_num_dense_hotr);
+        const int pw = p->opts.panel_cols;
+        const int cap = pw > 20480 ? pw : 20480;
+        const size_t budget = p->smem_optin > fa.sharedSizeBytes ? p->smem_optin - fa.sharedSizeBytes : 0;
+        const size_t base = hotr_smem(pw, 0, cap), per = (size_t)(pw / 32) * 8;
+        p->hotr_cap = cap;
+        p->hotr_pmax = budget > base + per ? (int)((budget - base) / per) : 0;
+        if (p->hotr_pmax > kMaxPanels) p->hotr_pmax = kMaxPanels;
+        allow_max_dynamic_smem((const void*)k_num_dense_hotr, p);
     }
     struct K {
         const void* f;
@@ -1259,6 +1559,14 @@ __global__ void k_copy_total(const Ctl* ctl, int which, long long* dst) { *dst =
 void launch_copy_total(const spgemm_plan* p, const WsPtrs& w, int which, long long* dst,
                        cudaStream_t s) {
     SPG_LAUNCH(p, K_GUARD, s, k_copy_total<<<1, 1, 0, s>>>(w.ctl, which, dst));
+}
+
+// Column ranges per row of the rank-compacted fp64 tier (work items per
+// row): opts.dense_splits when set, else 1.
+static int dense_splits(const spgemm_plan* p, int panels) {
+    int sp = p->opts.dense_splits > 0 ? p->opts.dense_splits : 1;
+    if (sp > panels) sp = panels > 0 ? panels : 1;
+    return sp;
 }
 
 void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, const long long* ip,
@@ -1325,12 +1633,25 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                        NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW, p->d32_ppp, 0));
     }
     if (w.bhot && w.bpanel) {
+        // rows with a cached bitmap: rank-compacted passes, split into
+        // p->opts-independent column ranges per row (dense_splits)
+        const bool hotr = w.rc_slot != nullptr && p->hotr_pmax >= 1;
+        if (hotr) {
+            const int pmax_r = p->hotr_pmax < w.panels ? p->hotr_pmax : w.panels;
+            const int splits = dense_splits(p, w.panels);
+            SPG_LAUNCH(p, K_NUM_DENSE64, s,
+                       k_num_dense_hotr<<<sms, kHotThreads, hotr_smem(PW, pmax_r, p->hotr_cap), s>>>(
+                           A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
+                           NB_DENSE64_0 + NB_DENSE_N, 7, w.bpanel, w.panels, PW, pmax_r,
+                           p->hotr_cap, w.hot_rank, w.hot_col, w.bhot, w.rc_slot, w.rc_bits,
+                           w.rc_nslots, w.rc_wpr, splits));
+        }
         SPG_LAUNCH(p, K_NUM_DENSE64, s,
                    k_num_dense_hot<<<sms * p->occ_num_dense_hot, kHotThreads, num_dense_hot_smem(p), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
                        NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW, p->hot_ppp,
                        w.hot_rank, w.hot_col, w.bhot, w.rc_slot, w.rc_bits, w.rc_nslots,
-                       w.rc_wpr));
+                       w.rc_wpr, hotr ? 1 : 0));
         return;
     }
     SPG_LAUNCH(p, K_NUM_DENSE64, s,

@@ -53,12 +53,16 @@ def sample_rows(ip, n, seed):
 def test_rmat20_full_size_parity():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     A_h = gen.rmat_symmetric(20, 16, 0.57, 0.19, 0.19, seed=2)
-    plan = Plan()
     A = DeviceCSR.from_host(A_h)
+    # the plan the benchmark times: the allocation phase's row bitmaps kept
+    # for every dense row that fits beside the output
+    import bench
+    plan = Plan(row_cache_mb=bench.row_cache_size(Plan(), A, A, A.device))
     ws = plan.workspace(A, A)
     blocks, ip_total, nnz_total = plan.spgemm_blocks(A, A, ws=ws)
     torch.cuda.synchronize()
     plan.check_status(ws, "A*A")
+    assert plan.row_cache_rows(A, A, ws) > 300000
     assert len(blocks) > 1                          # beyond int32 row pointers
     # every row's entry count against the oracle's allocation phase
     got_nnz = np.concatenate([np.diff(Cb.row_ptr.cpu().numpy().astype(np.int64))
@@ -73,8 +77,9 @@ def test_rmat20_full_size_parity():
     got = rows_of_blocks(blocks, rows)
     ref = oracle.spgemm(A_h, A_h, rows=rows)
     compare(got, ref, rows=np.arange(rows.size))
-    del blocks
+    del blocks, ws
     torch.cuda.empty_cache()
+    plan = Plan()
 
     # contraction S^T * A (the first factor of S^T A S)
     clusters = A_h.rows // 16

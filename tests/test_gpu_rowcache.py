@@ -51,10 +51,16 @@ def dense_rows(A, B, plan):
     return int(dense.sum()), int((dense & (ip > plan.opts["block_max_ip"])).sum()), nnz
 
 
-@pytest.mark.parametrize("bcols,cache_mb", [(70000, 64), (1_000_000, 1)])
-def test_row_cache_parity(bcols, cache_mb):
+@pytest.mark.parametrize("bcols,cache_mb,splits,panel", [(70000, 64, 1, 16384),
+                                                         (1_000_000, 1, 3, 16384),
+                                                         (70000, 64, 4, 1024),
+                                                         (70000, 64, 64, 1024)])
+def test_row_cache_parity(bcols, cache_mb, splits, panel):
+    """splits > 1: each heavy row of the fp64-bound tier is cut into that
+    many column ranges taken by different blocks (panel 1024: many passes
+    per range)."""
     A, B = operands(bcols)
-    plan = Plan(row_cache_mb=cache_mb)
+    plan = Plan(row_cache_mb=cache_mb, dense_splits=splits, panel_cols=panel)
     ndense, nbitmap, nnz = dense_rows(A, B, plan)
     na = np.diff(A.row_ptr)
     assert ndense > 20 and (na[nnz > 8192] <= 167).any() and (na[nnz > 8192] > 1024).any()
@@ -103,3 +109,33 @@ def test_row_cache_mismatch_reported():
     torch.cuda.synchronize()
     with pytest.raises(SpgemmError):
         plan.check_status(ws, "stale row cache")
+
+
+def test_row_cache_clustered_hot_columns():
+    """More hot columns inside one table panel than the rank-compacted fp64
+    tier has slots (2048): that pass is walked once per slot range."""
+    rng = np.random.default_rng(41)
+    rows, cols = 2000, 60000
+    warm = rng.choice(16384, size=3000, replace=False)
+    r, c = [], []
+    for i in range(rows):
+        cc = set(rng.choice(cols, size=rng.integers(5, 40), replace=False).tolist())
+        cc |= set(warm[rng.random(warm.size) < 250 / rows].tolist())
+        cc = np.array(sorted(cc))
+        r.append(np.full(cc.size, i))
+        c.append(cc)
+    r, c = np.concatenate(r), np.concatenate(c)
+    B = gen.csr_from_coo(rows, cols, r, c, gen.uniform_open_closed(rng, r.size))
+    counts = np.bincount(B.col, minlength=cols)
+    assert (counts[:16384] > 167).sum() > 2048
+    A = hub_matrix(20, rows, 42, heavy_rows={0, 5, 19}, heavy_len=1200, light_deg=300)
+    assert oracle.symbolic(A, B).max() > 8192
+    for splits in (1, 2):
+        plan = Plan(row_cache_mb=16, dense_splits=splits)
+        dA, dB = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
+        ws = plan.workspace(dA, dB)
+        C = plan.spgemm(dA, dB, ws=ws)
+        torch.cuda.synchronize()
+        plan.check_status(ws, "clustered hot columns")
+        assert plan.row_cache_rows(dA, dB, ws) > 0
+        compare(C.to_host(), oracle.spgemm(A, B))
