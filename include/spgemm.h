@@ -88,11 +88,13 @@ typedef struct {
                                  row's columns from its slot instead of marking every product
                                  again. Rows without a slot are unaffected. B.cols must be at
                                  most 1,572,864 for the cache to be used. */
-    int32_t dense_splits;     /* default 0 (= 1): work items per heavy row in the fp64-bound
-                                 dense tier for rows with a cached bitmap. Each item takes one
-                                 of that many consecutive column ranges of the row, so one row
-                                 runs on up to that many SMs at once; items write disjoint,
-                                 ordered slices of the row (no merge step). */
+    int32_t dense_splits;     /* default 0 (automatic): work items per heavy row in the
+                                 fp64-bound dense tier for rows with a cached bitmap. Each item
+                                 takes one of that many consecutive column ranges of the row,
+                                 so one row runs on up to that many SMs at once; items write
+                                 disjoint, ordered slices of the row (no merge step). 0 picks
+                                 one range per ~2M intermediate products (1 to 32 by the row's
+                                 product count); k > 0 fixes k ranges for every row. */
     int32_t reserved[7];
 } spgemm_opts;
 

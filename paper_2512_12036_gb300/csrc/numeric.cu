@@ -1163,6 +1163,15 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
 // values at the row's output offset plus the entries of the earlier ranges
 // (popcounts of the cached bitmap), so the pieces need no merge step: they
 // are column-disjoint and already in order.
+// Column ranges per row when opts.dense_splits is 0: by the row's bin q
+// (bins of the fp64 tier hold rows with IP in (2^(45-q), 2^(46-q)]), one
+// range per ~2M intermediate products, at most 32 and at most one per panel.
+__device__ __forceinline__ int auto_splits(int q, int P) {
+    const int L = 46 - q;                     // IP <= 2^L
+    int sp = L > 21 ? (L - 21 >= 5 ? 32 : 1 << (L - 21)) : 1;
+    return sp < P ? sp : (P > 0 ? P : 1);
+}
+
 constexpr int kHotrSlots = 2048;
 constexpr int kHotrStride = kHotrSlots + 1;   // copies of one slot in different banks
 constexpr int kHotrUnroll = 4;
@@ -1179,7 +1188,7 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hotr(
     float* vals = cp + kHotCopies * kHotrStride;                      // [cap]
     unsigned* bm = reinterpret_cast<unsigned*>(vals + cap);           // [pmax * PW / 32]
     int* rk = reinterpret_cast<int*>(bm + ((pmax * PW) >> 5));        // [pmax * PW / 32]
-    __shared__ int s_item, s_p1;
+    __shared__ int s_idx, s_g, s_S, s_p1;
     __shared__ int scratch[33];
     __shared__ int s_pc[kMaxPanels];    // entries of the item's panels
     __shared__ int s_ph[kMaxPanels];    // hot columns of the item's panels
@@ -1238,12 +1247,28 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hotr(
     };
 
     for (;;) {
-        if (t == 0) s_item = atomicAdd(&ctl->work[tier], 1);
+        if (t == 0) {
+            // item -> (bin, row of the bin, column range); bins are heaviest first
+            long long item = atomicAdd(&ctl->work[tier], 1);
+            int idx = end, g = 0, S = 1;
+            for (int b = bin_lo; b < bin_hi; ++b) {
+                const int n = ctl->bin_off[b + 1] - ctl->bin_off[b];
+                const int sb = splits > 0 ? splits : auto_splits(b - bin_lo, P);
+                if (item < (long long)n * sb) {
+                    idx = ctl->bin_off[b] + (int)(item / sb);
+                    g = (int)(item % sb);
+                    S = sb;
+                    break;
+                }
+                item -= (long long)n * sb;
+            }
+            s_idx = idx;
+            s_g = g;
+            s_S = S;
+        }
         __syncthreads();
-        const int item = s_item;
+        const int idx = s_idx, g = s_g, splits_row = s_S;
         __syncthreads();
-        const long long idx = begin + (long long)item / splits;
-        const int g = item % splits;
         if (idx >= end) break;
         const int r = map[idx];
         const int row = row_begin + r;
@@ -1252,7 +1277,8 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hotr(
         const int cslot = rc_slot[row];
         if (cslot < 0 || cslot >= rc_nslots) continue;     // k_num_dense_hot's row
         const unsigned* cbits = rc_bits + (size_t)cslot * rc_wpr;
-        const int gp0 = (int)((long long)P * g / splits), gp1 = (int)((long long)P * (g + 1) / splits);
+        const int gp0 = (int)((long long)P * g / splits_row);
+        const int gp1 = (int)((long long)P * (g + 1) / splits_row);
         if (gp0 >= gp1) continue;
         int rs, re;
         row_extent(A, row, rs, re, ctl);
@@ -1410,7 +1436,7 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hotr(
         if (t == 0) {
             int want = 0;
             for (int p = gp0; p < gp1; ++p) want += s_pc[p - gp0];
-            if (pass_base - item_base != want || (splits == 1 && pass_base != nnz_row))
+            if (pass_base - item_base != want || (splits_row == 1 && pass_base != nnz_row))
                 set_status(ctl, ST_INTERNAL);
         }
         __syncthreads();
@@ -1562,9 +1588,9 @@ void launch_copy_total(const spgemm_plan* p, const WsPtrs& w, int which, long lo
 }
 
 // Column ranges per row of the rank-compacted fp64 tier (work items per
-// row): opts.dense_splits when set, else 1.
+// row): opts.dense_splits when set, else 0 (the kernel's per-bin choice).
 static int dense_splits(const spgemm_plan* p, int panels) {
-    int sp = p->opts.dense_splits > 0 ? p->opts.dense_splits : 1;
+    int sp = p->opts.dense_splits;             // 0: chosen per row by the kernel
     if (sp > panels) sp = panels > 0 ? panels : 1;
     return sp;
 }

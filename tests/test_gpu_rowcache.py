@@ -54,11 +54,12 @@ def dense_rows(A, B, plan):
 @pytest.mark.parametrize("bcols,cache_mb,splits,panel", [(70000, 64, 1, 16384),
                                                          (1_000_000, 1, 3, 16384),
                                                          (70000, 64, 4, 1024),
-                                                         (70000, 64, 64, 1024)])
+                                                         (70000, 64, 64, 1024),
+                                                         (70000, 64, 0, 1024)])
 def test_row_cache_parity(bcols, cache_mb, splits, panel):
     """splits > 1: each heavy row of the fp64-bound tier is cut into that
     many column ranges taken by different blocks (panel 1024: many passes
-    per range)."""
+    per range); 0: ranges chosen per row by its product count."""
     A, B = operands(bcols)
     plan = Plan(row_cache_mb=cache_mb, dense_splits=splits, panel_cols=panel)
     ndense, nbitmap, nnz = dense_rows(A, B, plan)
