@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--dense-splits", type=int, default=None,
                     help="work items per heavy row in the fp64-bound dense tier")
+    ap.add_argument("--stage-b", action="store_true",
+                    help="allocation block tier with B segments staged in shared memory")
     ap.add_argument("--no-row-cache", action="store_true",
                     help="accumulation phase without the allocation phase's row bitmaps")
     ap.add_argument("--row-stride", type=int, default=1,
@@ -720,6 +722,8 @@ def run_ours(args):
     cache_mb = 0 if args.no_row_cache else row_cache_size(plan_c, L, A, dev)
     if args.dense_splits:
         opts["dense_splits"] = args.dense_splits
+    if args.stage_b:
+        opts["stage_b"] = 1
     plan = Plan(device=local, row_cache_mb=cache_mb, **opts)
     ws_aa = plan.workspace(L, A)
     ws_sa = plan_c.workspace(St, A)

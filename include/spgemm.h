@@ -93,9 +93,15 @@ typedef struct {
                                  takes one of that many consecutive column ranges of the row,
                                  so one row runs on up to that many SMs at once; items write
                                  disjoint, ordered slices of the row (no merge step). 0 picks
-                                 one range per ~2M intermediate products (1 to 32 by the row's
+                                 one range per ~512K intermediate products (1 to 32 by the row's
                                  product count); k > 0 fixes k ranges for every row. */
-    int32_t reserved[7];
+    int32_t stage_b;          /* default 0: when 1, rows of the allocation phase's block hash
+                                 tier with at most 8192 intermediate products first gather
+                                 their B row-pointer pairs and copy all their B segments into
+                                 shared memory (cp.async, double-buffered over rows), then
+                                 insert from there: a software form of the paper's near-memory
+                                 range-2 access (Section IV-D). Same results either way. */
+    int32_t reserved[6];
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;

@@ -44,6 +44,7 @@ struct spgemm_plan {
     size_t rank_budget;    // dynamic shared memory of the rank-compacted fp32 dense kernel
     int occ_num_rank;
     int hotr_cap, hotr_pmax;   // rank-compacted fp64 dense kernel: value slots, panels per pass
+    int occ_sym_staged;        // staged block hash tier of the allocation phase
 };
 
 namespace spg {

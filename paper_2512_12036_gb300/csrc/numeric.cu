@@ -1165,10 +1165,10 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
 // are column-disjoint and already in order.
 // Column ranges per row when opts.dense_splits is 0: by the row's bin q
 // (bins of the fp64 tier hold rows with IP in (2^(45-q), 2^(46-q)]), one
-// range per ~2M intermediate products, at most 32 and at most one per panel.
+// range per ~512K intermediate products, at most 32 and at most one per panel.
 __device__ __forceinline__ int auto_splits(int q, int P) {
     const int L = 46 - q;                     // IP <= 2^L
-    int sp = L > 21 ? (L - 21 >= 5 ? 32 : 1 << (L - 21)) : 1;
+    int sp = L > 19 ? (L - 19 >= 5 ? 32 : 1 << (L - 19)) : 1;
     return sp < P ? sp : (P > 0 ? P : 1);
 }
 

@@ -151,6 +151,124 @@ __global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev
 }
 
 // ---------------------------------------------------------------------------
+// Staged block hash tier: a software form of the near-memory range-2 access
+// the paper's AIA hardware performs (Section IV-D). For a row, the
+// row-pointer pairs of B selected by its A entries are gathered first, tile
+// by tile (the range-2 gather), then every B-row segment the row needs is
+// copied into shared memory with cp.async, so that the hash inserts read
+// their keys from shared memory in order, with no segment search and no
+// global load in the insert loop. Rows are double-buffered: the copies of
+// the next row are in flight while the current row is inserted. Rows of at
+// most kStageMax products (the bins of the block tier below 2^13) take this
+// kernel when opts.stage_b is set; the result is the same as k_sym_block's.
+constexpr int kStageMax = 8192;
+constexpr int kStageThreads = 512;
+
+__device__ __forceinline__ void cp_async4(int* smem, const int* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__global__ void __launch_bounds__(kStageThreads) k_sym_block_staged(CsrDev A, CsrDev B,
+                                                                    const long long* ip,
+                                                                    const int* map, Ctl* ctl,
+                                                                    int* row_nnz, int bin_lo,
+                                                                    int bin_hi, int tier) {
+    extern __shared__ int sm_staged[];
+    int* table = sm_staged;                        // [2 * kStageMax] keys
+    int* stage = sm_staged + 2 * kStageMax;        // [2][kStageMax] staged columns of B
+    __shared__ int s_idx;
+    __shared__ int s_off[kStageThreads + 1];       // prefix of the tile's segment lengths
+    __shared__ int s_bs[kStageThreads];
+    __shared__ int red[33];
+    const int t = threadIdx.x;
+    const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
+
+    auto next_row = [&]() -> int {
+        if (t == 0) {
+            const int idx = begin + atomicAdd(&ctl->work[tier], 1);
+            s_idx = idx < end ? map[idx] : -1;
+        }
+        __syncthreads();
+        const int row = s_idx;
+        __syncthreads();
+        return row;
+    };
+    // range-2 gather and copies of one row into stage buffer q; returns its
+    // products (rows above kStageMax products are flagged and cut short,
+    // which the host's bin choice rules out)
+    auto stage_row = [&](int row, int q) -> int {
+        int rs, re;
+        row_extent(A, row, rs, re, ctl);
+        int pos = 0;
+        for (int tb = rs; tb < re; tb += kStageThreads) {
+            const int j = tb + t;
+            int bs = 0, len = 0;
+            if (j < re) a_entry(A, B, j, bs, len, ctl);
+            int tot;
+            const int ex = block_excl_scan(len, red, &tot);
+            s_off[t] = ex;
+            s_bs[t] = bs;
+            if (t == 0) s_off[kStageThreads] = tot;
+            __syncthreads();
+            if (pos + tot > kStageMax) {
+                if (t == 0) set_status(ctl, ST_INTERNAL);
+                tot = kStageMax - pos;
+            }
+            int* dst = stage + q * kStageMax + pos;
+            for (int p = t; p < tot; p += kStageThreads) {
+                // entry holding product p: the last e with s_off[e] <= p
+                int lo = 0, hi = kStageThreads - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= p) lo = mid;
+                    else hi = mid - 1;
+                }
+                cp_async4(dst + p, B.col + s_bs[lo] + (p - s_off[lo]));
+            }
+            pos += tot;
+            __syncthreads();                       // s_off / s_bs are rewritten next tile
+        }
+        return pos;
+    };
+
+    int q = 0;
+    int row = next_row();
+    int n = row >= 0 ? stage_row(row, 0) : 0;
+    cp_async_commit();
+    while (row >= 0) {
+        const int row_next = next_row();
+        const int n_next = row_next >= 0 ? stage_row(row_next, q ^ 1) : 0;
+        cp_async_commit();
+        cp_async_wait<1>();                        // this row's copies (the older group)
+        __syncthreads();
+        const long long want = 2 * ip[row];
+        int bits = 6;
+        while (bits < 14 && (1ll << bits) < want) ++bits;
+        const int T = 1 << bits;
+        for (int i = t; i < T; i += kStageThreads) table[i] = kEmpty;
+        __syncthreads();
+        const int* keys = stage + q * kStageMax;
+        int cnt = 0;
+        for (int p = t; p < n; p += kStageThreads) {
+            const int key = keys[p];
+            if (key_ok(key, B, ctl)) cnt += hash_insert(table, bits, key, ctl);
+        }
+        cnt = block_sum(cnt, red);
+        if (t == 0) row_nnz[row] = cnt;
+        row = row_next;
+        n = n_next;
+        q ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // With a row bitmap cache (rc_slot != nullptr), a row that fits one pass and
 // whose entry count puts it in a dense accumulation tier (nnz > cache_min)
 // takes the next free slot and leaves its column bitmap there for the
@@ -268,7 +386,13 @@ static size_t sym_dense_smem(const spgemm_plan* p) {
     return words * 4;
 }
 
+static size_t staged_smem() { return sizeof(int) * 4 * (size_t)kStageMax; }
+
 void occupancy_symbolic(spgemm_plan* p) {
+    allow_max_dynamic_smem((const void*)k_sym_block_staged, p);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_staged, k_sym_block_staged,
+                                                  kStageThreads, staged_smem());
+    if (p->occ_sym_staged < 1) p->occ_sym_staged = 1;
     const size_t sw = (size_t)kWarpsPerBlockSW * kWarpTableSym * 4;
     const size_t sb = (size_t)pow2_ceil(2u * (unsigned)p->opts.block_max_ip) * 4;
     const size_t sd = sym_dense_smem(p);
@@ -310,9 +434,25 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     const unsigned tb = pow2_ceil(2u * (unsigned)p->opts.block_max_ip);
     int max_bits = 0;
     while ((1u << max_bits) < tb) ++max_bits;
+    // staged tier (opts.stage_b): the block-tier bins whose rows hold at most
+    // kStageMax products; bin SB_BLOCK0 + q holds IP <= 2^(Lmax - q)
+    int staged_lo = SB_BLOCK0 + SB_BLOCK_N;
+    if (p->opts.stage_b) {
+        const int Lmax = log2_ceil_ll(p->opts.block_max_ip);
+        for (int q = 0; q < SB_BLOCK_N; ++q)
+            if ((1ll << (Lmax - q > 0 ? Lmax - q : 0)) <= kStageMax ||
+                (q == 0 && p->opts.block_max_ip <= kStageMax)) {
+                staged_lo = SB_BLOCK0 + q;
+                break;
+            }
+    }
     SPG_LAUNCH(p, K_SYM_BLOCK, s,
                k_sym_block<<<sms * p->occ_sym_block, kSymBlockThreads, (size_t)tb * 4, s>>>(
-                   A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, SB_BLOCK0 + SB_BLOCK_N, 0, max_bits));
+                   A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, staged_lo, 0, max_bits));
+    if (staged_lo < SB_BLOCK0 + SB_BLOCK_N)
+        SPG_LAUNCH(p, K_SYM_BLOCK, s,
+                   k_sym_block_staged<<<sms * p->occ_sym_staged, kStageThreads, staged_smem(), s>>>(
+                       A, B, ip, w.map, w.ctl, row_nnz, staged_lo, SB_BLOCK0 + SB_BLOCK_N, 2));
     if (B.cols <= kNarrowCols)
         SPG_LAUNCH(p, K_SYM_NARROW, s,
                    k_sym_narrow<<<sms * 8, kNarrowWarps * 32, 0, s>>>(A, B, w.map, w.ctl, row_nnz,
