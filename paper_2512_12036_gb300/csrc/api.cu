@@ -41,6 +41,10 @@ WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long lon
         off = align256(off + sizeof(int) * (size_t)b_cols);
         L.bhot = off;
         off = align256(off + sizeof(int) * (size_t)b_nnz);
+        L.bhv = off;
+        off = align256(off + 8 * (size_t)b_nnz);
+        L.bcv = off;
+        off = align256(off + 8 * (size_t)b_nnz);
     }
     const long long wpr = (b_cols + 31) / 32;
     if (p->opts.row_cache_mb > 0 && m > 0 && wpr > 0 && wpr <= kRowCacheMaxWords) {
@@ -75,6 +79,8 @@ WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols) {
     w.hot_rank = L.has_hot ? (int*)(b + L.hot_rank) : nullptr;
     w.hot_col = L.has_hot ? (int*)(b + L.hot_col) : nullptr;
     w.bhot = L.has_hot ? (int*)(b + L.bhot) : nullptr;
+    w.bhv = L.has_hot ? (int2*)(b + L.bhv) : nullptr;
+    w.bcv = L.has_hot ? (int2*)(b + L.bcv) : nullptr;
     w.rc_slot = L.rc_nslots > 0 ? (int*)(b + L.rc_slot) : nullptr;
     w.rc_bits = L.rc_nslots > 0 ? (unsigned*)(b + L.rc_bits) : nullptr;
     w.rc_nslots = L.rc_nslots;

@@ -99,6 +99,8 @@ struct WsLayout {
     size_t hot_rank = 0;     // int32 [B.cols+1]  exclusive prefix of the hot flags
     size_t hot_col = 0;      // int32 [B.cols]    hot columns in ascending order
     size_t bhot = 0;         // int32 [B.nnz]     each B entry's column, or (sign bit | hot rank)
+    size_t bhv = 0;          // int2 [B.nnz]      (bhot, value bits) per B entry, packed per call
+    size_t bcv = 0;          // int2 [B.nnz]      (column, value bits) per B entry, packed per call
     size_t rc_slot = 0;      // int32 [m]         row -> bitmap slot (-1: none)
     size_t rc_bits = 0;      // u32 [rc_nslots][rc_wpr] row bitmaps of the allocation phase
     int rc_nslots = 0, rc_wpr = 0;
@@ -120,6 +122,8 @@ struct WsPtrs {
     int* hot_rank;
     int* hot_col;
     int* bhot;
+    int2* bhv;
+    int2* bcv;
     int* rc_slot;            // nullptr: no row bitmap cache
     unsigned* rc_bits;
     int rc_nslots, rc_wpr;

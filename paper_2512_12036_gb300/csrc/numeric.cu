@@ -716,7 +716,8 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                                                                    int pmax, int cap,
                                                                    const int* rc_slot,
                                                                    const unsigned* rc_bits,
-                                                                   int rc_nslots, int rc_wpr) {
+                                                                   int rc_nslots, int rc_wpr,
+                                                                   const int2* bcv) {
     constexpr int kT = kD32Threads;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int RW = (pmax * PW) >> 5;                  // words of the widest pass
@@ -743,7 +744,10 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
         if (kk < (unsigned)span) atomicOr(&bm[kk >> 5], 1u << (kk & 31));
         else if (key_in(key, B, ctl)) set_status(ctl, ST_INTERNAL);
     };
-    auto load = [&](int q) { return KeyVal{B.col[q], B.val[q]}; };
+    auto load = [&](int q) {
+        const int2 v = bcv[q];
+        return KeyVal{v.x, __int_as_float(v.y)};
+    };
     auto add = [&](KeyVal kv, float a) {
         const unsigned kk = (unsigned)kv.key - (unsigned)c0;
         if (kk >= (unsigned)span) {
@@ -922,7 +926,7 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                                                                   const int* tab, int P, int PW,
                                                                   int ppp, const int* hot_rank,
                                                                   const int* hot_col,
-                                                                  const int* bhot,
+                                                                  const int2* bhv,
                                                                   const int* rc_slot,
                                                                   const unsigned* rc_bits,
                                                                   int rc_nslots, int rc_wpr,
@@ -957,7 +961,10 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
     // the row's cached column bitmap (allocation phase), or nullptr: with it
     // the sub-pass's bitmap words are copied in and products mark nothing
     const unsigned* cbits = nullptr;
-    auto load = [&](int q) { return KeyVal{bhot[q], B.val[q]}; };
+    auto load = [&](int q) {
+        const int2 v = bhv[q];
+        return KeyVal{v.x, __int_as_float(v.y)};
+    };
     // one bitmap OR and one fp32 add per product, hot or cold, on selected
     // addresses (a hot product marks its slot, a cold one its column), so the
     // warp does not diverge into two instruction sequences
@@ -1174,12 +1181,15 @@ __device__ __forceinline__ int auto_splits(int q, int P) {
 
 constexpr int kHotrSlots = 2048;
 constexpr int kHotrStride = kHotrSlots + 1;   // copies of one slot in different banks
-constexpr int kHotrUnroll = 4;
+#ifndef SPG_HOTR_UNROLL
+#define SPG_HOTR_UNROLL 4
+#endif
+constexpr int kHotrUnroll = SPG_HOTR_UNROLL;   // products per warp step batch
 
 __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hotr(
     CsrDev A, CsrDev B, const int* map, Ctl* ctl, const int* rptC, int row_begin, int* colC,
     float* valC, int bin_lo, int bin_hi, int tier, const int* tab, int P, int PW, int pmax,
-    int cap, const int* hot_rank, const int* hot_col, const int* bhot, const int* rc_slot,
+    int cap, const int* hot_rank, const int* hot_col, const int2* bhv, const int* rc_slot,
     const unsigned* rc_bits, int rc_nslots, int rc_wpr, int splits) {
     constexpr int kT = kHotThreads;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -1208,7 +1218,10 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hotr(
     // of the pass [hrp0, hrp1); cold: this walk adds cold products
     int c0 = 0, span = 0, hr0 = 0, nhs = 0, hrp0 = 0, hrp1 = 0;
     bool cold = true;
-    auto load = [&](int q) { return KeyVal{bhot[q], B.val[q]}; };
+    auto load = [&](int q) {
+        const int2 v = bhv[q];
+        return KeyVal{v.x, __int_as_float(v.y)};
+    };
     // one instruction sequence for hot and cold products: both compute a
     // cold rank (a hot one on word 0) and add once at a selected address
     auto apply = [&](KeyVal kv, float a, int seg) {
@@ -1570,6 +1583,20 @@ void launch_bpanel(const spgemm_plan* p, const CsrDev& B, const WsPtrs& w, cudaS
     SPG_LAUNCH(p, K_BPANEL, s, k_bpanel<<<(int)blocks, 256, 0, s>>>(B, w.panels, w.panel_cols, w.bpanel, w.ctl));
 }
 
+// (column word, value) of every B entry packed into one 8-byte record per
+// entry, so the dense tiers read a product's column and value with one
+// vector load: bcv holds the column, bhv the column word of the fp64 tier
+// (column, or sign bit | hot rank). Rebuilt by every accumulation call, so
+// B's values may change between calls.
+__global__ void k_pack_b(CsrDev B, const int* bhot, int2* bhv, int2* bcv) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < B.nnz;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int v = __float_as_int(B.val[j]);
+        bcv[j] = make_int2(B.col[j], v);
+        bhv[j] = make_int2(bhot[j], v);
+    }
+}
+
 // Output-capacity guard of the graph-capturable path: empties every bin
 // when C does not fit (or its row pointers overflowed), so no tier writes.
 __global__ void k_cap_guard(const int* rptC, int n, long long capacity, Ctl* ctl) {
@@ -1638,6 +1665,8 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                k_num_block<double><<<sms * p->occ_num_block64, kNumBlockThreads, num_block_smem(p, 8), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits));
     const int PW = w.panel_cols;
+    if (w.bhv && w.bpanel && B.nnz > 0)
+        SPG_LAUNCH(p, K_HOT, s, k_pack_b<<<sms * 8, 256, 0, s>>>(B, w.bhot, w.bhv, w.bcv));
     const int pmax = w.panels < kRankPanels ? w.panels : kRankPanels;
     const int cap = w.bpanel ? rank_cap(p, pmax, PW) : 0;
     if (w.bpanel && cap >= 1024) {
@@ -1647,7 +1676,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                    k_num_dense_rank<<<sms * p->occ_num_rank, kD32Threads, rank_smem(p, pmax, PW), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
                        NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW, pmax, cap,
-                       w.rc_slot, w.rc_bits, w.rc_nslots, w.rc_wpr));
+                       w.rc_slot, w.rc_bits, w.rc_nslots, w.rc_wpr, w.bcv));
         SPG_LAUNCH(p, K_NUM_DENSE32, s,
                    k_num_dense<0, kD32Threads><<<sms * p->occ_num_dense32, kD32Threads, num_dense_smem(p, 0), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
@@ -1669,14 +1698,14 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                        k_num_dense_hotr<<<sms, kHotThreads, hotr_smem(PW, pmax_r, p->hotr_cap), s>>>(
                            A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
                            NB_DENSE64_0 + NB_DENSE_N, 7, w.bpanel, w.panels, PW, pmax_r,
-                           p->hotr_cap, w.hot_rank, w.hot_col, w.bhot, w.rc_slot, w.rc_bits,
+                           p->hotr_cap, w.hot_rank, w.hot_col, w.bhv, w.rc_slot, w.rc_bits,
                            w.rc_nslots, w.rc_wpr, splits));
         }
         SPG_LAUNCH(p, K_NUM_DENSE64, s,
                    k_num_dense_hot<<<sms * p->occ_num_dense_hot, kHotThreads, num_dense_hot_smem(p), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
                        NB_DENSE64_0 + NB_DENSE_N, 5, w.bpanel, w.panels, PW, p->hot_ppp,
-                       w.hot_rank, w.hot_col, w.bhot, w.rc_slot, w.rc_bits, w.rc_nslots,
+                       w.hot_rank, w.hot_col, w.bhv, w.rc_slot, w.rc_bits, w.rc_nslots,
                        w.rc_wpr, hotr ? 1 : 0));
         return;
     }
