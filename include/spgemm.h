@@ -93,8 +93,9 @@ typedef struct {
                                  takes one of that many consecutive column ranges of the row,
                                  so one row runs on up to that many SMs at once; items write
                                  disjoint, ordered slices of the row (no merge step). 0 picks
-                                 one range per ~512K intermediate products (1 to 32 by the row's
-                                 product count); k > 0 fixes k ranges for every row. */
+                                 one range per 128K intermediate products, at most 8 (1 to 8
+                                 by the row's product count); k > 0 fixes k ranges for every
+                                 row. */
     int32_t stage_b;          /* default 0: when 1, rows of the allocation phase's block hash
                                  tier with at most 8192 intermediate products first gather
                                  their B row-pointer pairs and copy all their B segments into

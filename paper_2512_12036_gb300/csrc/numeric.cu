@@ -1171,20 +1171,22 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
 // (popcounts of the cached bitmap), so the pieces need no merge step: they
 // are column-disjoint and already in order.
 // Column ranges per row when opts.dense_splits is 0: by the row's bin q
-// (bins of the fp64 tier hold rows with IP in (2^(45-q), 2^(46-q)]), one
-// range per ~512K intermediate products, at most 32 and at most one per panel.
+// (bins of the fp64 tier hold rows with IP in (2^(45-q), 2^(46-q)]): one
+// range per 128K intermediate products, at most 8 and at most one per panel.
+// (On the R-MAT scale 20 product, whose tier rows hold 1M-22M products, 8
+// ranges for every row measured best: 1 / 4 / 8 / 16 / 32 ranges gave 410 /
+// 262 / 249 / 252 / 269 ms; one range per 2M products gave 301 ms.)
 __device__ __forceinline__ int auto_splits(int q, int P) {
     const int L = 46 - q;                     // IP <= 2^L
-    int sp = L > 19 ? (L - 19 >= 5 ? 32 : 1 << (L - 19)) : 1;
+    const int sp = L >= 20 ? 8 : (L > 17 ? 1 << (L - 17) : 1);
     return sp < P ? sp : (P > 0 ? P : 1);
 }
 
 constexpr int kHotrSlots = 2048;
 constexpr int kHotrStride = kHotrSlots + 1;   // copies of one slot in different banks
-#ifndef SPG_HOTR_UNROLL
-#define SPG_HOTR_UNROLL 4
-#endif
-constexpr int kHotrUnroll = SPG_HOTR_UNROLL;   // products per warp step batch
+// products per warp step batch: 2 / 3 / 4 measured 254 / 248 / 268 ms on the
+// R-MAT scale 20 product (4 spills registers at the 64-register limit)
+constexpr int kHotrUnroll = 3;
 
 __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hotr(
     CsrDev A, CsrDev B, const int* map, Ctl* ctl, const int* rptC, int row_begin, int* colC,
