@@ -369,8 +369,9 @@ def pattern_pruned_layer(A, plan, device, d: int = 256, dout: int = 256, k: int 
     return {"n": A.rows, "d": d, "dout": dout, "k": k, "forward_ms": fwd_ms, "backward_ms": bwd_ms,
             "spgemm_products": int(ip),
             "forward_gflops_all": (2.0 * ip / 1e9 + dense_gflop) / (fwd_ms / 1e3),
-            "note": "forward: TopK, A*TopK(X) (hash SpGEMM), dense C*W (cuBLAS fp32); backward: "
-                    "dY*W^T and C^T*dY (cuBLAS), gather at C's pattern, spgemm_backward, "
+            "note": "forward: TopK, A*TopK(X) (hash SpGEMM), dense C*W (spgemm_dense_gemm, "
+                    "fp32 CUDA-core GEMM); backward: dY*W^T and C^T*dY (spgemm_dense_gemm, "
+                    "split-K with fp64 partial sums), gather at C's pattern, spgemm_backward, "
                     "scatter into dX (M_k-masked)"}
 
 

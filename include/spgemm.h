@@ -222,6 +222,28 @@ int spgemm_backward(const spgemm_plan* plan, const spgemm_csr* A, const spgemm_c
                     const float* dC, float* dA, float* dB, void* ws, size_t ws_bytes,
                     void* stream);
 
+/* Dense fp32 GEMM for the pruned GNN layer's dense products (Section IV-C,
+ * Eq. 1: the aggregated features times W_l; Eq. 3 and the weight gradient:
+ * dY * W_l^T and C^T * dY):
+ *   C[M x N] = op(A)[M x K] * op(B)[K x N]
+ * All matrices row-major fp32 on the plan's device with leading dimensions
+ * (elements): op(A) = A (M x K, lda >= K) or, with trans_a = 1, A^T of a
+ * stored K x M matrix (lda >= M); op(B) = B (K x N, ldb >= N) or, with
+ * trans_b = 1, B^T of a stored N x K matrix (ldb >= K); ldc >= N. C is
+ * overwritten (K = 0 gives zeros). Products are fp32 fused multiply-adds;
+ * a long reduction with few output tiles (K deep, e.g. C^T * dY over all
+ * rows of a graph) is split over blocks along K when the caller passes a
+ * workspace of spgemm_dense_gemm_workspace_bytes (256-byte aligned; 0 bytes
+ * when no split is needed): each block's fp32 partial sum is added into an
+ * fp64 accumulator there and rounded once. Without one, each output tile
+ * runs the whole reduction in one block. Returns SPGEMM_ERR_INVALID for
+ * bad sizes or pointers; does not synchronise. */
+int spgemm_dense_gemm_workspace_bytes(const spgemm_plan* plan, int32_t M, int32_t N, int32_t K,
+                                      size_t* bytes);
+int spgemm_dense_gemm(const spgemm_plan* plan, int32_t M, int32_t N, int32_t K, const float* A,
+                      int64_t lda, int32_t trans_a, const float* B, int64_t ldb, int32_t trans_b,
+                      float* C, int64_t ldc, void* ws, size_t ws_bytes, void* stream);
+
 /* Allocation callback for spgemm(): must return device buffers of nnz
  * entries (col and val) and 0, or nonzero to abort. */
 typedef int (*spgemm_alloc_fn)(void* ctx, int64_t nnz, int32_t** col, float** val);

@@ -80,6 +80,9 @@ PROTOTYPES = {
                                           c_vp, _P(c_i64), c_vp]),
     "spgemm_select_columns": (ctypes.c_int, [c_vp, _CSR, c_vp, c_sz, c_vp, c_vp, c_vp, c_vp, c_vp,
                                              c_vp, _P(c_i64), c_vp]),
+    "spgemm_dense_gemm_workspace_bytes": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, _P(c_sz)]),
+    "spgemm_dense_gemm": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i64, c_i32, c_vp, c_i64,
+                                         c_i32, c_vp, c_i64, c_vp, c_sz, c_vp]),
     "spgemm_status": (ctypes.c_int, [c_vp, c_vp, c_vp, _P(ctypes.c_int)]),
     "spgemm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "spgemm_profile_enable": (ctypes.c_int, [c_vp, ctypes.c_int]),

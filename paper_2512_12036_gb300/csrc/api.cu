@@ -111,7 +111,7 @@ const char* const kKernelNames[K_NUM_KERNELS] = {
     "group_scatter", "scan_part", "scan_top", "scan_final", "reset_flag", "bpanel", "sym_esc",
     "sym_warp", "sym_block", "sym_dense", "num_esc", "num_warp32", "num_warp64", "num_block32",
     "num_block64", "num_dense32", "num_dense64", "backward", "guard", "mcl", "hot", "layer",
-    "sym_narrow", "num_narrow"};
+    "sym_narrow", "num_narrow", "gemm"};
 
 void prof_begin(const spgemm_plan* p, int kid, cudaStream_t s) {
     (void)kid;

@@ -15,7 +15,7 @@ enum KernelId : int {
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_FINAL, K_RESET, K_BPANEL, K_SYM_ESC, K_SYM_WARP, K_SYM_BLOCK,
     K_SYM_DENSE, K_NUM_ESC, K_NUM_WARP32, K_NUM_WARP64, K_NUM_BLOCK32, K_NUM_BLOCK64,
     K_NUM_DENSE32, K_NUM_DENSE64, K_BWD, K_GUARD, K_MCL, K_HOT, K_LAYER, K_SYM_NARROW,
-    K_NUM_NARROW, K_NUM_KERNELS
+    K_NUM_NARROW, K_GEMM, K_NUM_KERNELS
 };
 extern const char* const kKernelNames[K_NUM_KERNELS];
 
@@ -195,6 +195,13 @@ void launch_gather_dense(const spgemm_plan* p, const CsrDev& M, const float* D, 
 void launch_mcl_step(const spgemm_plan* p, const CsrDev& E, float theta, int k, double r,
                      int order, const WsPtrs& w, int* rpt_out, int* col_out, float* val_out,
                      cudaStream_t s);
+
+// Dense fp32 GEMM C = op(A) * op(B) (row-major, leading dimensions); with
+// acc (fp64, M*N) the reduction is split over ksplit blocks along K.
+void launch_sgemm(const spgemm_plan* p, int M, int N, int K, const float* A, long long lda,
+                  bool ta, const float* B, long long ldb, bool tb, float* C, long long ldc,
+                  double* acc, int ksplit, cudaStream_t s);
+int gemm_ksplit(const spgemm_plan* p, int M, int N, int K);
 
 void init_occupancy(spgemm_plan* p);
 // Lets kernel f take as much dynamic shared memory as the device allows

@@ -6,8 +6,8 @@ A by it with the hash-based SpGEMM, and applies the dense weight. The
 backward follows Eq. 3: the gradient of A * TopK(X) is dY * W^T read at that
 product's pattern, spgemm_backward turns it into A^T * dC on TopK's pattern
 (the M_k-masked gradient of Eq. 3), and a scatter lays it into the dense
-dX. The products with the dense W are plain dense GEMMs (cuBLAS through
-torch.matmul, fp32); every sparse step runs in this library's kernels.
+dX. The products with the dense W (C*W, dY*W^T, C^T*dY) are this library's
+fp32 GEMM (spgemm_dense_gemm); every step of the layer runs in its kernels.
 
 GCN, GIN and GraphSAGE layers are compositions of that step (the graph
 operator each uses is built by the caller: Ahat = D^-1/2 (A+I) D^-1/2 for
@@ -79,6 +79,62 @@ def gather_dense(M: DeviceCSR, D: torch.Tensor, plan: Plan, ws: torch.Tensor | N
     return out
 
 
+def dense_mm(A: torch.Tensor, B: torch.Tensor, plan: Plan, trans_a: bool = False,
+             trans_b: bool = False, stream=None) -> torch.Tensor:
+    """op(A) @ op(B) for row-major fp32 device matrices with unit column
+    stride, through spgemm_dense_gemm (a split-K workspace is allocated when
+    the reduction is long)."""
+    for T in (A, B):
+        if T.dtype != torch.float32 or T.dim() != 2 or (T.numel() > 0 and T.stride(1) != 1):
+            raise ValueError("operands must be 2-D fp32 tensors with unit column stride")
+    M, K = (A.shape[1], A.shape[0]) if trans_a else (A.shape[0], A.shape[1])
+    Kb, N = (B.shape[1], B.shape[0]) if trans_b else (B.shape[0], B.shape[1])
+    if K != Kb:
+        raise ValueError(f"inner dimensions differ: {K} vs {Kb}")
+    C = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    L = _lib.lib()
+    nb = ctypes.c_size_t()
+    check(L.spgemm_dense_gemm_workspace_bytes(plan.handle, M, N, K, ctypes.byref(nb)),
+          "spgemm_dense_gemm_workspace_bytes")
+    ws = None
+    if nb.value:
+        raw = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device=A.device)
+        off = (-raw.data_ptr()) % 256
+        ws = raw[off:off + int(nb.value)]
+    lda = A.stride(0) if A.numel() else A.shape[1]
+    ldb = B.stride(0) if B.numel() else B.shape[1]
+    check(L.spgemm_dense_gemm(plan.handle, M, N, K, _ptr(A), lda, int(trans_a), _ptr(B), ldb,
+                              int(trans_b), _ptr(C), N, _ptr(ws) if ws is not None else None,
+                              int(nb.value) if ws is not None else 0, _stream(stream)),
+          "spgemm_dense_gemm")
+    return C
+
+
+class DenseLinear(torch.autograd.Function):
+    """Y = X @ W with both gradients (dX = dY W^T, dW = X^T dY) through
+    spgemm_dense_gemm."""
+
+    @staticmethod
+    def forward(ctx, X, W, plan: Plan):
+        X = X.detach().contiguous()
+        W = W.detach().contiguous()
+        ctx.save_for_backward(X, W)
+        ctx.plan = plan
+        return dense_mm(X, W, plan)
+
+    @staticmethod
+    def backward(ctx, dY):
+        X, W = ctx.saved_tensors
+        dY = dY.contiguous()
+        dX = dense_mm(dY, W, ctx.plan, trans_b=True) if ctx.needs_input_grad[0] else None
+        dW = dense_mm(X, dY, ctx.plan, trans_a=True) if ctx.needs_input_grad[1] else None
+        return dX, dW, None
+
+
+def dense_linear(X: torch.Tensor, W: torch.Tensor, plan: Plan) -> torch.Tensor:
+    return DenseLinear.apply(X, W, plan)
+
+
 class PrunedAggregation(torch.autograd.Function):
     """Y = A * TopK(X, k) * W (Eq. 1) with the backward of Eq. 3."""
 
@@ -93,7 +149,7 @@ class PrunedAggregation(torch.autograd.Function):
         plan.check_status(ws, "pruned layer forward")
         ctx.save_for_backward(Cd, W)
         ctx.A, ctx.T, ctx.C, ctx.plan, ctx.shape = A, T, C, plan, X.shape
-        return Cd @ W
+        return dense_mm(Cd, W, plan)
 
     @staticmethod
     def backward(ctx, dY):
@@ -102,10 +158,10 @@ class PrunedAggregation(torch.autograd.Function):
         dY = dY.contiguous()
         dX = dW = None
         if ctx.needs_input_grad[1]:
-            dW = Cd.t() @ dY
+            dW = dense_mm(Cd, dY, plan, trans_a=True)
         if ctx.needs_input_grad[0]:
             ws = _small_ws(plan, dY.device)
-            dC = gather_dense(ctx.C, dY @ W.t(), plan, ws=ws)
+            dC = gather_dense(ctx.C, dense_mm(dY, W, plan, trans_b=True), plan, ws=ws)
             bws = plan.backward_workspace(ctx.A, ctx.T)
             _, dT = plan.backward(ctx.A, ctx.T, ctx.C, dC, need_dA=False, need_dB=True, ws=bws)
             plan.check_status(bws, "pruned layer backward")
@@ -155,7 +211,8 @@ class PrunedGIN(torch.nn.Module):
         self.plan = plan or Plan(device=torch.device(device).index)
 
     def forward(self, A_gin: DeviceCSR, X: torch.Tensor) -> torch.Tensor:
-        return torch.relu(pruned_aggregation(A_gin, X, self.W1, self.k, self.plan)) @ self.W2
+        return dense_linear(torch.relu(pruned_aggregation(A_gin, X, self.W1, self.k, self.plan)),
+                            self.W2, self.plan)
 
 
 class PrunedSAGE(torch.nn.Module):
