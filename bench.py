@@ -273,7 +273,7 @@ def pattern_batched(num_graphs: int, device):
     import torch
 
     from paper_2512_12036_gb300 import DeviceCSR, Plan, gen
-    from paper_2512_12036_gb300.batched import autotune, time_graph
+    from paper_2512_12036_gb300.batched import SEARCH_SPACE, autotune, time_graph
 
     t0 = time.perf_counter()
     batch = gen.gnn_batch(num_graphs, seed=5)
@@ -322,7 +322,12 @@ def pattern_batched(num_graphs: int, device):
             "batched": {"forward_ms": ms_fwd, "backward_ms": ms_bwd,
                         "forward_gflops": gflop / (ms_fwd / 1e3),
                         "p50_ms": ms_fwd, "p99_ms": ms_fwd, "launch": "one CUDA graph replay",
-                        "autotuned_opts": opts, "candidates_ms": timings},
+                        "autotuned_opts": opts, "candidates_ms": timings,
+                        "search": "coordinate descent over " + ", ".join(
+                            f"{n} ({len(v)} values)" for n, v in SEARCH_SPACE),
+                        "default_ms": timings.get("default"),
+                        "gain_vs_default": (timings["default"] / min(timings.values())
+                                            if timings.get("default") else None)},
             "pruned_gcn_layer": layer,
             "plain": {"total_ms": 1e3 * plain_s, "gflops": gflop / plain_s,
                       "p50_ms": 1e3 * _pct(done_at, 0.5), "p99_ms": 1e3 * _pct(done_at, 0.99)},

@@ -102,7 +102,14 @@ typedef struct {
                                  shared memory (cp.async, double-buffered over rows), then
                                  insert from there: a software form of the paper's near-memory
                                  range-2 access (Section IV-D). Same results either way. */
-    int32_t reserved[6];
+    int32_t narrow_warps;     /* default 0 (= 8): warps per block (1..16) of the narrow tiers
+                                 (B with at most 1024 columns: one warp per row with a dense
+                                 per-warp accumulator over B's columns) */
+    int32_t narrow_max_ip;    /* default 0 (= 32768): largest IP of a row in the narrow tiers */
+    int32_t hash_load_pct;    /* default 0 (= 50): target load of the hash tiers' tables in
+                                 percent (25..90); a row's table is the smallest power of two
+                                 holding its keys at that load */
+    int32_t reserved[3];
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;

@@ -38,11 +38,11 @@ class CsrStruct(ctypes.Structure):
 
 OPT_FIELDS = ["fp32_max_terms", "esc_max", "warp_max_ip", "block_max_ip", "warp_max_nnz",
               "block_max_nnz", "panel_cols", "row_cache_mb", "dense_splits",
-              "stage_b"]
+              "stage_b", "narrow_warps", "narrow_max_ip", "hash_load_pct"]
 
 
 class OptsStruct(ctypes.Structure):
-    _fields_ = [(n, c_i32) for n in OPT_FIELDS] + [("reserved", c_i32 * 6)]
+    _fields_ = [(n, c_i32) for n in OPT_FIELDS] + [("reserved", c_i32 * 3)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_int, c_vp, c_i64, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp))

@@ -1,5 +1,5 @@
 """Batched products under a captured CUDA graph, and the autotuner that picks
-the row-tier thresholds for a batch.
+the row-tier thresholds, hash-table load and narrow-tier shape for a batch.
 
 Many small, uneven problems C_b = A_b * B_b are one product of the
 block-diagonal stack of the A_b with the row stack of the B_b (the stacked
@@ -122,22 +122,37 @@ class BatchedSpGEMM:
 # Autotuner
 # ---------------------------------------------------------------------------
 
+# The autotuner's search space: the row-tier thresholds (the role of the
+# paper's Table 1 group boundaries), the hash tables' target load (table
+# sizes), and the narrow tiers' warps per block and row limit. The
+# accumulation-precision rule (fp32_max_terms) is not a knob: every point
+# meets the same tolerance.
+BASE_OPTS = {"esc_max": 32, "warp_max_ip": 1024, "block_max_ip": 16384, "warp_max_nnz": 512,
+             "block_max_nnz": 8192, "hash_load_pct": 50, "narrow_warps": 8,
+             "narrow_max_ip": 32768}
+SEARCH_SPACE = [
+    ("narrow_warps", [{"narrow_warps": w} for w in (4, 8, 16)]),
+    ("narrow_max_ip", [{"narrow_max_ip": v} for v in (4096, 32768, 131072)]),
+    ("tiers", [{}, {"esc_max": 16},
+               {"warp_max_ip": 256, "warp_max_nnz": 128},
+               {"warp_max_ip": 512, "warp_max_nnz": 256},
+               {"block_max_ip": 4096, "block_max_nnz": 2048},
+               {"warp_max_nnz": 256, "block_max_nnz": 4096}]),
+    ("hash_load_pct", [{"hash_load_pct": v} for v in (35, 50, 70)]),
+]
+
+
 def candidate_opts() -> list[dict]:
-    """Row-tier thresholds and table sizes to try (all keep the same
-    accumulation-precision rule, so every candidate meets the tolerance)."""
-    base = {"esc_max": 32, "warp_max_ip": 1024, "block_max_ip": 16384, "warp_max_nnz": 512,
-            "block_max_nnz": 8192}
-    grid = [
-        {},
-        {"esc_max": 16},
-        {"warp_max_ip": 256, "warp_max_nnz": 128},
-        {"warp_max_ip": 512, "warp_max_nnz": 256},
-        {"block_max_ip": 4096, "block_max_nnz": 2048},
-        {"warp_max_ip": 256, "warp_max_nnz": 128, "block_max_ip": 4096, "block_max_nnz": 2048},
-        {"warp_max_nnz": 256, "block_max_nnz": 4096},
-        {"esc_max": 16, "warp_max_ip": 512, "warp_max_nnz": 256},
-    ]
-    return [dict(base, **g) for g in grid]
+    """Every point the search can visit (each knob's values on the defaults)."""
+    out, seen = [], set()
+    for _, values in SEARCH_SPACE:
+        for v in values:
+            c = dict(BASE_OPTS, **v)
+            key = tuple(sorted(c.items()))
+            if key not in seen:
+                seen.add(key)
+                out.append(c)
+    return out
 
 
 def time_graph(bs: BatchedSpGEMM, reps: int = 5) -> float:
@@ -156,20 +171,37 @@ def time_graph(bs: BatchedSpGEMM, reps: int = 5) -> float:
 
 def autotune(A: DeviceCSR, B: DeviceCSR, candidates: list[dict] | None = None, reps: int = 5,
              capacity: int | None = None):
-    """Time every candidate configuration as a captured graph on this batch;
-    return (best BatchedSpGEMM, best opts, {index: ms})."""
-    cands = candidates or candidate_opts()
+    """Pick options for this batch by timing captured graphs. Without
+    ``candidates``: coordinate descent over SEARCH_SPACE (one knob group at a
+    time, each value tried on the best point so far, the fastest kept).
+    Returns (best BatchedSpGEMM, best opts, {label: ms}) with every timed
+    point in the dict."""
     timings = {}
     best = None
-    for q, opts in enumerate(cands):
+
+    def trial(label, opts):
+        nonlocal best, capacity
         bs = BatchedSpGEMM(A, B, Plan(device=A.device.index, **opts), capacity=capacity)
         if capacity is None:
             capacity = bs.capacity
         bs.capture()
         ms = time_graph(bs, reps)
-        timings[q] = ms
+        timings[label] = ms
         if best is None or ms < best[0]:
-            best = (ms, bs, opts)
+            best = (ms, bs, dict(opts))
         else:
             del bs
+
+    if candidates is not None:
+        for q, opts in enumerate(candidates):
+            trial(str(q), opts)
+        return best[1], best[2], timings
+    trial("default", dict(BASE_OPTS))
+    for name, values in SEARCH_SPACE:
+        base = dict(best[2])
+        for v in values:
+            opts = dict(base, **v)
+            if opts == base:
+                continue
+            trial(f"{name}:{','.join(f'{k}={x}' for k, x in sorted(v.items())) or 'default'}", opts)
     return best[1], best[2], timings

@@ -249,6 +249,10 @@ int spgemm_plan_create(spgemm_plan** out, const spgemm_opts* opts, int device) {
     if (o.fp32_max_terms < 0) return SPGEMM_ERR_INVALID;
     if (o.row_cache_mb < 0 || o.dense_splits < 0 || o.dense_splits > 64) return SPGEMM_ERR_INVALID;
     if (o.stage_b != 0 && o.stage_b != 1) return SPGEMM_ERR_INVALID;
+    if (o.narrow_warps < 0 || o.narrow_warps > kNarrowMaxWarps || o.narrow_max_ip < 0)
+        return SPGEMM_ERR_INVALID;
+    if (o.hash_load_pct != 0 && (o.hash_load_pct < 25 || o.hash_load_pct > 90))
+        return SPGEMM_ERR_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return SPGEMM_ERR_CUDA;

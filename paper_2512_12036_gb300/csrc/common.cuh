@@ -103,6 +103,14 @@ __host__ __device__ __forceinline__ int log2_ceil_ll(long long x) {
     return l;
 }
 
+// Bits of a hash table for `keys` keys at a target load of load_pct percent:
+// the smallest power of two 2^b >= keys * 100 / load_pct, b in [lo, hi].
+__host__ __device__ __forceinline__ int table_bits(long long keys, int load_pct, int lo, int hi) {
+    int b = lo;
+    while (b < hi && (1ll << b) * load_pct < 100 * keys) ++b;
+    return b;
+}
+
 // Multiplicative (Fibonacci) hashing into a power-of-two table of 2^bits
 // slots: the top bits of key * floor(2^32 / golden ratio).
 __device__ __forceinline__ unsigned hash_slot(int key, int bits) {

@@ -168,7 +168,7 @@ __device__ __forceinline__ int bin_of(const GroupArgs& g, int r, bool settle) {
             return kSkipBin;
         }
         if (ip <= o.esc_max && na <= o.esc_max) return SB_ESC;
-        if (g.bcols <= kNarrowCols && ip <= kNarrowMaxIP) return SB_NARROW;
+        if (g.bcols <= kNarrowCols && ip <= narrow_max_ip(o)) return SB_NARROW;
         if (ip <= o.warp_max_ip) return SB_WARP;
         const int L = log2_ceil_ll(ip);
         if (ip <= o.block_max_ip) {
@@ -181,7 +181,7 @@ __device__ __forceinline__ int bin_of(const GroupArgs& g, int r, bool settle) {
     if (nnz <= 0) return kSkipBin;
     const bool f64 = na > o.fp32_max_terms && ip > o.fp32_max_terms;
     if (ip <= o.esc_max && na <= o.esc_max) return NB_ESC;
-    if (g.bcols <= kNarrowCols && ip <= kNarrowMaxIP) return f64 ? NB_NARROW64 : NB_NARROW32;
+    if (g.bcols <= kNarrowCols && ip <= narrow_max_ip(o)) return f64 ? NB_NARROW64 : NB_NARROW32;
     if (nnz <= o.warp_max_nnz && ip <= 16ll * o.warp_max_nnz) return f64 ? NB_WARP64 : NB_WARP32;
     if (nnz <= o.block_max_nnz) return f64 ? NB_BLOCK64 : NB_BLOCK32;
     const int L = log2_ceil_ll(ip);

@@ -79,7 +79,18 @@ enum : int {
 // kNarrowMaxIP products take one warp each with a dense per-warp
 // accumulator over all of B's columns (no hashing, no sort).
 constexpr int kNarrowCols = 1024;
-constexpr long long kNarrowMaxIP = 32768;
+constexpr long long kNarrowMaxIP = 32768;   // default of opts.narrow_max_ip
+constexpr int kNarrowWarpsDefault = 8;      // default of opts.narrow_warps
+constexpr int kNarrowMaxWarps = 16;
+inline int narrow_warps(const spgemm_plan* p) {
+    return p->opts.narrow_warps > 0 ? p->opts.narrow_warps : kNarrowWarpsDefault;
+}
+inline int hash_load(const spgemm_plan* p) {
+    return p->opts.hash_load_pct > 0 ? p->opts.hash_load_pct : 50;
+}
+__host__ __device__ inline long long narrow_max_ip(const spgemm_opts& o) {
+    return o.narrow_max_ip > 0 ? o.narrow_max_ip : kNarrowMaxIP;
+}
 
 // Backward tiers (grouping phase 3, by nnz of the row of C): dense lookup
 // when B has few columns, warp hash, block hash, dense column panels.

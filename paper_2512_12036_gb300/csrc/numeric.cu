@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kWarpsPerBlockNW * 32) k_num_warp(CsrDev A, Cs
                                                                     const int* map, Ctl* ctl,
                                                                     const int* rptC, int row_begin,
                                                                     int* colC, float* valC,
-                                                                    int bin) {
+                                                                    int bin, int load_pct) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     Acc* vals = reinterpret_cast<Acc*>(sm_raw) + warp * kWarpTableNum;
@@ -249,8 +249,7 @@ __global__ void __launch_bounds__(kWarpsPerBlockNW * 32) k_num_warp(CsrDev A, Cs
         const int row = row_begin + r;
         const int out = rptC[r];
         const int nnz_row = rptC[r + 1] - out;
-        int bits = 5;
-        while (bits < kMaxBits && (1 << bits) < 2 * nnz_row) ++bits;
+        const int bits = table_bits(nnz_row, load_pct, 5, kMaxBits);
         const int T = 1 << bits;
         for (int t = lane; t < T; t += 32) {
             keys[t] = kEmpty;
@@ -300,19 +299,19 @@ __global__ void __launch_bounds__(kWarpsPerBlockNW * 32) k_num_warp(CsrDev A, Cs
 // a 32-word bitmap; lane l owns word l, so a warp scan of the popcounts
 // writes the row in column order with no sort. Touched entries are cleared
 // on the way out, so the array stays zero between rows.
-constexpr int kNarrowWarps = 8;
-
 template <typename Acc>
-__global__ void __launch_bounds__(kNarrowWarps * 32) k_num_narrow(CsrDev A, CsrDev B,
-                                                                  const int* map, Ctl* ctl,
-                                                                  const int* rptC, int row_begin,
-                                                                  int* colC, float* valC, int bin,
-                                                                  int ncols_pad) {
+__global__ void __launch_bounds__(kNarrowMaxWarps * 32) k_num_narrow(CsrDev A, CsrDev B,
+                                                                     const int* map, Ctl* ctl,
+                                                                     const int* rptC, int row_begin,
+                                                                     int* colC, float* valC,
+                                                                     int bin, int ncols_pad) {
+    // per warp: a dense accumulator over B's columns, then a 32-word bitmap
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    __shared__ unsigned bmw[kNarrowWarps][32];
     const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int nwarps = blockDim.x >> 5;
     Acc* dense = reinterpret_cast<Acc*>(sm_raw) + warp * ncols_pad;
-    unsigned* bm = bmw[warp];
+    unsigned* bm = reinterpret_cast<unsigned*>(reinterpret_cast<Acc*>(sm_raw) + nwarps * ncols_pad) +
+                   warp * 32;
     for (int c = lane; c < ncols_pad; c += 32) dense[c] = Acc(0);
     bm[lane] = 0u;
     __syncwarp();
@@ -361,7 +360,8 @@ __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev
                                                                 const int* map, Ctl* ctl,
                                                                 const int* rptC, int row_begin,
                                                                 int* colC, float* valC, int bin,
-                                                                int tier, int max_bits) {
+                                                                int tier, int max_bits,
+                                                                int load_pct) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     Acc* vals = reinterpret_cast<Acc*>(sm_raw);
     int* keys = reinterpret_cast<int*>(sm_raw + sizeof(Acc) * (1u << max_bits));
@@ -381,8 +381,7 @@ __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev
         const int row = row_begin + r;
         const int out = rptC[r];
         const int nnz_row = rptC[r + 1] - out;
-        int bits = 6;
-        while (bits < max_bits && (1 << bits) < 2 * nnz_row) ++bits;
+        const int bits = table_bits(nnz_row, load_pct, 6, max_bits);
         const int T = 1 << bits;
         for (int t = threadIdx.x; t < T; t += blockDim.x) {
             keys[t] = kEmpty;
@@ -1644,28 +1643,32 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     SPG_LAUNCH(p, K_NUM_ESC, s, k_num_esc<<<sms * 8, 256, 0, s>>>(A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_ESC));
     if (B.cols <= kNarrowCols) {
         const int pad = (B.cols + 31) & ~31;
+        const int nwp = narrow_warps(p);
+        const int grid = sms * (64 / nwp > 1 ? 64 / nwp : 1);
         SPG_LAUNCH(p, K_NUM_NARROW, s,
-                   k_num_narrow<float><<<sms * 8, kNarrowWarps * 32, (size_t)kNarrowWarps * pad * 4, s>>>(
+                   k_num_narrow<float><<<grid, nwp * 32, (size_t)nwp * (pad * 4 + 128), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_NARROW32, pad));
         SPG_LAUNCH(p, K_NUM_NARROW, s,
-                   k_num_narrow<double><<<sms * 8, kNarrowWarps * 32, (size_t)kNarrowWarps * pad * 8, s>>>(
+                   k_num_narrow<double><<<grid, nwp * 32, (size_t)nwp * (pad * 8 + 128), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_NARROW64, pad));
     }
     SPG_LAUNCH(p, K_NUM_WARP32, s,
                k_num_warp<float><<<sms * p->occ_num_warp32, kWarpsPerBlockNW * 32, num_warp_smem(4), s>>>(
-                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP32));
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP32, hash_load(p)));
     SPG_LAUNCH(p, K_NUM_WARP64, s,
                k_num_warp<double><<<sms * p->occ_num_warp64, kWarpsPerBlockNW * 32, num_warp_smem(8), s>>>(
-                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP64));
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP64, hash_load(p)));
     const unsigned tb = pow2_ceil(2u * (unsigned)p->opts.block_max_nnz);
     int max_bits = 0;
     while ((1u << max_bits) < tb) ++max_bits;
     SPG_LAUNCH(p, K_NUM_BLOCK32, s,
                k_num_block<float><<<sms * p->occ_num_block32, kNumBlockThreads, num_block_smem(p, 4), s>>>(
-                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK32, 2, max_bits));
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK32, 2, max_bits,
+                   hash_load(p)));
     SPG_LAUNCH(p, K_NUM_BLOCK64, s,
                k_num_block<double><<<sms * p->occ_num_block64, kNumBlockThreads, num_block_smem(p, 8), s>>>(
-                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits));
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits,
+                   hash_load(p)));
     const int PW = w.panel_cols;
     if (w.bhv && w.bpanel && B.nnz > 0)
         SPG_LAUNCH(p, K_HOT, s, k_pack_b<<<sms * 8, 256, 0, s>>>(B, w.bhot, w.bhv, w.bcv));

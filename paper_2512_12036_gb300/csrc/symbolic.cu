@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(256) k_sym_esc(CsrDev A, CsrDev B, const int* 
 __global__ void __launch_bounds__(kWarpsPerBlockSW * 32) k_sym_warp(CsrDev A, CsrDev B,
                                                                     const long long* ip,
                                                                     const int* map, Ctl* ctl,
-                                                                    int* row_nnz, int bin) {
+                                                                    int* row_nnz, int bin,
+                                                                    int load_pct) {
     extern __shared__ int sm_tables[];
     int* table = sm_tables + (threadIdx.x >> 5) * kWarpTableSym;
     const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
@@ -91,9 +92,7 @@ __global__ void __launch_bounds__(kWarpsPerBlockSW * 32) k_sym_warp(CsrDev A, Cs
     constexpr int kMaxBits = 11;   // 2048 slots
     for (int idx = begin + gw; idx < end; idx += nw) {
         const int row = map[idx];
-        const long long want = 2 * ip[row];
-        int bits = 5;
-        while (bits < kMaxBits && (1ll << bits) < want) ++bits;
+        const int bits = table_bits(ip[row], load_pct, 5, kMaxBits);
         const int T = 1 << bits;
         for (int t = lane; t < T; t += 32) table[t] = kEmpty;
         __syncwarp();
@@ -116,7 +115,7 @@ __global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev
                                                                 const int* map, Ctl* ctl,
                                                                 int* row_nnz, int bin_lo,
                                                                 int bin_hi, int tier,
-                                                                int max_bits) {
+                                                                int max_bits, int load_pct) {
     extern __shared__ int table[];
     __shared__ int s_idx;
     __shared__ int red[33];
@@ -129,9 +128,7 @@ __global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev
         __syncthreads();
         if (idx >= end) break;
         const int row = map[idx];
-        const long long want = 2 * ip[row];
-        int bits = 6;
-        while (bits < max_bits && (1ll << bits) < want) ++bits;
+        const int bits = table_bits(ip[row], load_pct, 6, max_bits);
         const int T = 1 << bits;
         for (int t = threadIdx.x; t < T; t += blockDim.x) table[t] = kEmpty;
         __syncthreads();
@@ -178,7 +175,8 @@ __global__ void __launch_bounds__(kStageThreads) k_sym_block_staged(CsrDev A, Cs
                                                                     const long long* ip,
                                                                     const int* map, Ctl* ctl,
                                                                     int* row_nnz, int bin_lo,
-                                                                    int bin_hi, int tier) {
+                                                                    int bin_hi, int tier,
+                                                                    int load_pct) {
     extern __shared__ int sm_staged[];
     int* table = sm_staged;                        // [2 * kStageMax] keys
     int* stage = sm_staged + 2 * kStageMax;        // [2][kStageMax] staged columns of B
@@ -247,9 +245,7 @@ __global__ void __launch_bounds__(kStageThreads) k_sym_block_staged(CsrDev A, Cs
         cp_async_commit();
         cp_async_wait<1>();                        // this row's copies (the older group)
         __syncthreads();
-        const long long want = 2 * ip[row];
-        int bits = 6;
-        while (bits < 14 && (1ll << bits) < want) ++bits;
+        const int bits = table_bits(ip[row], load_pct, 6, 14);
         const int T = 1 << bits;
         for (int i = t; i < T; i += kStageThreads) table[i] = kEmpty;
         __syncthreads();
@@ -347,14 +343,12 @@ __global__ void k_rc_reset(int* rc_slot, int m, Ctl* ctl) {
 // Narrow B (<= kNarrowCols columns): one warp per row marks the row's
 // columns in a per-warp bitmap of 32 words (word w holds columns 32w..32w+31)
 // and counts them; no table, no probing.
-constexpr int kNarrowWarps = 8;
-
-__global__ void __launch_bounds__(kNarrowWarps * 32) k_sym_narrow(CsrDev A, CsrDev B,
-                                                                  const int* map, Ctl* ctl,
-                                                                  int* row_nnz, int bin) {
-    __shared__ unsigned bmw[kNarrowWarps][32];
+__global__ void __launch_bounds__(kNarrowMaxWarps * 32) k_sym_narrow(CsrDev A, CsrDev B,
+                                                                     const int* map, Ctl* ctl,
+                                                                     int* row_nnz, int bin) {
+    extern __shared__ unsigned bmw[];           // 32 words per warp
     const int lane = lane_id();
-    unsigned* bm = bmw[threadIdx.x >> 5];
+    unsigned* bm = bmw + (threadIdx.x >> 5) * 32;
     bm[lane] = 0u;
     __syncwarp();
     const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
@@ -430,7 +424,7 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     const size_t sw = (size_t)kWarpsPerBlockSW * kWarpTableSym * 4;
     SPG_LAUNCH(p, K_SYM_WARP, s,
                k_sym_warp<<<sms * p->occ_sym_warp, kWarpsPerBlockSW * 32, sw, s>>>(
-                   A, B, ip, w.map, w.ctl, row_nnz, SB_WARP));
+                   A, B, ip, w.map, w.ctl, row_nnz, SB_WARP, hash_load(p)));
     const unsigned tb = pow2_ceil(2u * (unsigned)p->opts.block_max_ip);
     int max_bits = 0;
     while ((1u << max_bits) < tb) ++max_bits;
@@ -448,15 +442,18 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     }
     SPG_LAUNCH(p, K_SYM_BLOCK, s,
                k_sym_block<<<sms * p->occ_sym_block, kSymBlockThreads, (size_t)tb * 4, s>>>(
-                   A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, staged_lo, 0, max_bits));
+                   A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, staged_lo, 0, max_bits,
+                   hash_load(p)));
     if (staged_lo < SB_BLOCK0 + SB_BLOCK_N)
         SPG_LAUNCH(p, K_SYM_BLOCK, s,
                    k_sym_block_staged<<<sms * p->occ_sym_staged, kStageThreads, staged_smem(), s>>>(
-                       A, B, ip, w.map, w.ctl, row_nnz, staged_lo, SB_BLOCK0 + SB_BLOCK_N, 2));
+                       A, B, ip, w.map, w.ctl, row_nnz, staged_lo, SB_BLOCK0 + SB_BLOCK_N, 2,
+                       hash_load(p)));
     if (B.cols <= kNarrowCols)
         SPG_LAUNCH(p, K_SYM_NARROW, s,
-                   k_sym_narrow<<<sms * 8, kNarrowWarps * 32, 0, s>>>(A, B, w.map, w.ctl, row_nnz,
-                                                                     SB_NARROW));
+                   k_sym_narrow<<<sms * (64 / narrow_warps(p) > 1 ? 64 / narrow_warps(p) : 1),
+                                  narrow_warps(p) * 32, (size_t)narrow_warps(p) * 128, s>>>(
+                       A, B, w.map, w.ctl, row_nnz, SB_NARROW));
     const size_t sd = sym_dense_smem(p);
     SPG_LAUNCH(p, K_SYM_DENSE, s,
                k_sym_dense<<<sms * p->occ_sym_dense, kSymDenseThreads, sd, s>>>(

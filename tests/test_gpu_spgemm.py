@@ -500,3 +500,19 @@ def test_contraction_full_StAS(plan, scale, clusters):
     # the contraction preserves the total weight of the graph
     assert abs(float(C2_h.val.astype(np.float64).sum()) - float(A_h.val.astype(np.float64).sum())) \
         <= 2e-5 * float(np.abs(A_h.val.astype(np.float64)).sum())
+
+
+@pytest.mark.parametrize("opts", [{"narrow_warps": 4}, {"narrow_warps": 16},
+                                  {"narrow_max_ip": 4096}, {"narrow_max_ip": 131072},
+                                  {"hash_load_pct": 35}, {"hash_load_pct": 70},
+                                  {"hash_load_pct": 90, "warp_max_nnz": 128}])
+def test_tuning_knobs_keep_results(opts):
+    """The autotuner's knobs (narrow-tier warps and row limit, hash-table
+    load) change schedules and table sizes only: results match the oracle."""
+    plan = Plan(**opts)
+    # narrow B (the GNN feature shape) and a wide B that fills the hash tiers
+    X = gen.topk_rows(np.random.default_rng(3).normal(size=(3000, 256)).astype(np.float32), 32)
+    Ah = gen.sym_normalised_adjacency(3000, 24.0, np.random.default_rng(4))
+    check_product(plan, Ah, X)
+    A = gen.rmat_symmetric(12, 8, seed=6)
+    check_product(plan, A, A)

@@ -55,8 +55,15 @@ def test_autotuner_candidates_are_valid_options():
         assert set(c) <= set(_lib.OPT_FIELDS)
         assert 0 < c["esc_max"] <= c["warp_max_nnz"] <= c["block_max_nnz"]
         assert c["warp_max_ip"] <= c["block_max_ip"]
+        assert 25 <= c["hash_load_pct"] <= 90 and 1 <= c["narrow_warps"] <= 16
         # the precision rule is not a tuning knob: every candidate keeps it
         assert "fp32_max_terms" not in c
+    # every knob group varies something
+    from paper_2512_12036_gb300.batched import SEARCH_SPACE
+    assert {n for n, _ in SEARCH_SPACE} >= {"tiers", "hash_load_pct", "narrow_warps",
+                                            "narrow_max_ip"}
+    for _, values in SEARCH_SPACE:
+        assert len(values) >= 2
 
 
 def test_interpret_picks_largest_then_smaller_index():
