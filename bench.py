@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--dense-splits", type=int, default=None,
                     help="work items per heavy row in the fp64-bound dense tier")
+    ap.add_argument("--only", choices=["batched", "served", "mcl", "er4096"], default=None,
+                    help="run one pattern measurement alone (profiling); no benchmark line")
     ap.add_argument("--stage-b", action="store_true",
                     help="allocation block tier with B segments staged in shared memory")
     ap.add_argument("--no-row-cache", action="store_true",
@@ -963,10 +965,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_one_pattern(args):
+    """One pattern measurement alone (for profiling a pattern's kernels);
+    prints its record as one JSON line. Not the benchmark line."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    if args.only == "batched":
+        rec = pattern_batched(args.gnn_graphs, dev)
+    elif args.only == "served":
+        rec = pattern_served(args.served_requests, dev)
+    elif args.only == "mcl":
+        rec = pattern_mcl(dev)
+    else:
+        rec = pattern_er4096(dev)
+    print(json.dumps({"pattern": args.only, **rec}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_one_pattern(args)
     else:
         run_ours(args)
 

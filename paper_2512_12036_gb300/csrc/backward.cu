@@ -44,27 +44,54 @@ __global__ void k_bwd_convert(const double* src, float* dst, long long n) {
         dst[i] = (float)src[i];
 }
 
-// One warp handles A entry j of row i: lanes walk B_k, look dC up with
-// `look(col) -> (found, g)`, reduce dA in fp64, add dB contributions.
-// `in_range(col)` restricts the walk to the current panel (true otherwise).
-template <class Look>
-__device__ __forceinline__ double bwd_entry(const BwdArgs& x, int j, int ts, int te, Look&& look) {
+// A warp handles A entries [j0, j0 + cnt) of one row (cnt <= 32): lane l
+// first gathers entry j0 + l's B segment (seg(j, ts, te)) and value, so the
+// 32 entries' index loads are in flight together; then the entries are
+// walked four at a time (independent loads and reductions overlap), each
+// entry's products spread over the lanes, dA reduced in fp64; lane l
+// returns entry j0 + l's sum (the caller writes them, coalesced). dB
+// contributions go out as fp64 atomics on the way.
+template <class Seg, class Look>
+__device__ __forceinline__ double bwd_chunk(const BwdArgs& x, int j0, int cnt, Seg&& seg,
+                                            Look&& look) {
     const int lane = lane_id();
-    const float a = x.A.val[j];
-    double acc = 0.0;
-    for (int t = ts + lane; t < te; t += 32) {
-        const int c = x.B.col[t];
-        float g = 0.f;
-        if ((unsigned)c < (unsigned)x.B.cols) {
-            if (!look(c, g)) set_status(x.ctl, ST_INVALID);   // C lacks a product's column
-        } else {
-            set_status(x.ctl, ST_INVALID);
-        }
-        const float b = x.B.val[t];
-        acc += (double)g * (double)b;
-        if (x.dB64) atomicAdd(&x.dB64[t], (double)a * (double)g);
+    int ts = 0, te = 0;
+    float a = 0.f;
+    if (lane < cnt) {
+        seg(j0 + lane, ts, te);
+        a = x.A.val[j0 + lane];
     }
-    return warp_sum(acc);
+    double mine = 0.0;
+    for (int q = 0; q < cnt; q += 4) {
+        double acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int qq = q + u;
+            const int sts = __shfl_sync(kFull, ts, qq & 31);
+            const int ste = qq < cnt ? __shfl_sync(kFull, te, qq & 31) : sts;
+            const float sa = __shfl_sync(kFull, a, qq & 31);
+            acc[u] = 0.0;
+            for (int t = sts + lane; t < ste; t += 32) {
+                const int c = x.B.col[t];
+                float g = 0.f;
+                if ((unsigned)c < (unsigned)x.B.cols) {
+                    if (!look(c, g)) set_status(x.ctl, ST_INVALID);   // C lacks a product's column
+                } else {
+                    set_status(x.ctl, ST_INVALID);
+                }
+                acc[u] += (double)g * (double)x.B.val[t];
+                if (x.dB64) atomicAdd(&x.dB64[t], (double)sa * (double)g);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(kFull, acc[u], o);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (lane == q + u) mine = acc[u];
+    }
+    return mine;
 }
 
 // ---------------------------------------------------------------------------
@@ -90,14 +117,20 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_bwd_dense(BwdArgs x, int bin
         __syncwarp();
         int rs, re;
         row_extent(x.A, i, rs, re, x.ctl);
-        for (int j = rs; j < re; ++j) {
-            int bs, len;
-            a_entry(x.A, x.B, j, bs, len, x.ctl);
-            const double d = bwd_entry(x, j, bs, bs + len, [&](int c, float& g) {
-                g = dense[c];
-                return true;
-            });
-            if (x.dA && lane == 0) x.dA[j] = (float)d;
+        for (int j0 = rs; j0 < re; j0 += 32) {
+            const double d = bwd_chunk(
+                x, j0, re - j0 < 32 ? re - j0 : 32,
+                [&](int j, int& ts, int& te) {
+                    int bs, len;
+                    a_entry(x.A, x.B, j, bs, len, x.ctl);
+                    ts = bs;
+                    te = bs + len;
+                },
+                [&](int c, float& g) {
+                    g = dense[c];
+                    return true;
+                });
+            if (x.dA && j0 + lane < re) x.dA[j0 + lane] = (float)d;
         }
         __syncwarp();
         for (int q = cs + lane; q < ce; q += 32) {
@@ -160,13 +193,17 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_bwd_warp(BwdArgs x, int bin)
         __syncwarp();
         int rs, re;
         row_extent(x.A, i, rs, re, x.ctl);
-        for (int j = rs; j < re; ++j) {
-            int bs, len;
-            a_entry(x.A, x.B, j, bs, len, x.ctl);
-            const double d = bwd_entry(x, j, bs, bs + len, [&](int c, float& g) {
-                return bwd_lookup(keys, vals, bits, c, g);
-            });
-            if (x.dA && lane == 0) x.dA[j] = (float)d;
+        for (int j0 = rs; j0 < re; j0 += 32) {
+            const double d = bwd_chunk(
+                x, j0, re - j0 < 32 ? re - j0 : 32,
+                [&](int j, int& ts, int& te) {
+                    int bs, len;
+                    a_entry(x.A, x.B, j, bs, len, x.ctl);
+                    ts = bs;
+                    te = bs + len;
+                },
+                [&](int c, float& g) { return bwd_lookup(keys, vals, bits, c, g); });
+            if (x.dA && j0 + lane < re) x.dA[j0 + lane] = (float)d;
         }
         __syncwarp();
     }
@@ -198,13 +235,17 @@ __global__ void __launch_bounds__(kBwdBlockThreads) k_bwd_block(BwdArgs x, int b
         __syncthreads();
         int rs, re;
         row_extent(x.A, i, rs, re, x.ctl);
-        for (int j = rs + warp; j < re; j += nwarps) {
-            int bs, len;
-            a_entry(x.A, x.B, j, bs, len, x.ctl);
-            const double d = bwd_entry(x, j, bs, bs + len, [&](int c, float& g) {
-                return bwd_lookup(keys, vals, bits, c, g);
-            });
-            if (x.dA && lane == 0) x.dA[j] = (float)d;
+        for (int j0 = rs + 32 * warp; j0 < re; j0 += 32 * nwarps) {
+            const double d = bwd_chunk(
+                x, j0, re - j0 < 32 ? re - j0 : 32,
+                [&](int j, int& ts, int& te) {
+                    int bs, len;
+                    a_entry(x.A, x.B, j, bs, len, x.ctl);
+                    ts = bs;
+                    te = bs + len;
+                },
+                [&](int c, float& g) { return bwd_lookup(keys, vals, bits, c, g); });
+            if (x.dA && j0 + lane < re) x.dA[j0 + lane] = (float)d;
         }
         __syncthreads();
     }
@@ -257,29 +298,35 @@ __global__ void __launch_bounds__(kBwdBlockThreads) k_bwd_panel(BwdArgs x, int b
             __syncthreads();
             const int p0 = pass * per;
             const int p1 = p0 + per < x.P ? p0 + per : x.P;
-            for (int j = rs + warp; j < re; j += nwarps) {
-                int bs, len;
-                a_entry(x.A, x.B, j, bs, len, x.ctl);
-                int ts = bs, te = bs + len;
-                if (use_tab && len > 0) {
-                    const int* tk = x.tab + (long long)x.A.col[j] * (x.P + 1);
-                    ts = tk[p0];
-                    te = tk[p1];
-                    if (ts < bs || te < ts || te > bs + len) {
-                        set_status(x.ctl, ST_INTERNAL);
-                        ts = te = bs;
-                    }
-                }
-                const double d = bwd_entry(x, j, ts, te, [&](int c, float& g) {
-                    const int cc = c - c0;
-                    if (cc < 0 || cc >= kBwdPanel) {
-                        g = 0.f;           // outside this pass (filtered walk of an unsorted row)
+            for (int j0 = rs + 32 * warp; j0 < re; j0 += 32 * nwarps) {
+                const double d = bwd_chunk(
+                    x, j0, re - j0 < 32 ? re - j0 : 32,
+                    [&](int j, int& ts, int& te) {
+                        int bs, len;
+                        a_entry(x.A, x.B, j, bs, len, x.ctl);
+                        ts = bs;
+                        te = bs + len;
+                        if (use_tab && len > 0) {
+                            const int* tk = x.tab + (long long)x.A.col[j] * (x.P + 1);
+                            ts = tk[p0];
+                            te = tk[p1];
+                            if (ts < bs || te < ts || te > bs + len) {
+                                set_status(x.ctl, ST_INTERNAL);
+                                ts = te = bs;
+                            }
+                        }
+                    },
+                    [&](int c, float& g) {
+                        const int cc = c - c0;
+                        if (cc < 0 || cc >= kBwdPanel) {
+                            g = 0.f;       // outside this pass (filtered walk of an unsorted row)
+                            return true;
+                        }
+                        g = dense[cc];
                         return true;
-                    }
-                    g = dense[cc];
-                    return true;
-                });
-                if (lane == 0 && d != 0.0) dA64[j] += d;   // one warp owns entry j
+                    });
+                // one warp owns entries [j0, j0 + 32)
+                if (j0 + lane < re && d != 0.0) dA64[j0 + lane] += d;
             }
             __syncthreads();
             for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
