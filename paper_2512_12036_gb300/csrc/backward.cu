@@ -48,9 +48,19 @@ __global__ void k_bwd_convert(const double* src, float* dst, long long n) {
 // first gathers entry j0 + l's B segment (seg(j, ts, te)) and value, so the
 // 32 entries' index loads are in flight together; then the entries are
 // walked four at a time (independent loads and reductions overlap), each
-// entry's products spread over the lanes, dA reduced in fp64; lane l
-// returns entry j0 + l's sum (the caller writes them, coalesced). dB
-// contributions go out as fp64 atomics on the way.
+// entry's products spread over the lanes; lane l returns entry j0 + l's dA
+// (the caller writes them, coalesced). dB contributions go out as fp64
+// atomics on the way.
+//
+// Precision without fp64 arithmetic on the SM (GB300's fp64 pipe is slow):
+// a segment of L products is summed as 32 per-lane fp32 partial sums of at
+// most ceil(L/32) products and a 5-level fp32 tree, so every product meets
+// at most ceil(L/32) + 6 roundings (its own product included): the error
+// stays within gamma_(ceil(L/32)+6) * sum|g b| <= 1e-5 * sum|g b| for L up to
+// kBwdF32Len; longer segments are summed in fp64. A dB term a*g is rounded
+// once to fp32 (relative error 2^-24) and added in fp64.
+constexpr int kBwdF32Len = 32 * 160;
+
 template <class Seg, class Look>
 __device__ __forceinline__ double bwd_chunk(const BwdArgs& x, int j0, int cnt, Seg&& seg,
                                             Look&& look) {
@@ -61,26 +71,41 @@ __device__ __forceinline__ double bwd_chunk(const BwdArgs& x, int j0, int cnt, S
         seg(j0 + lane, ts, te);
         a = x.A.val[j0 + lane];
     }
+    auto lookup = [&](int t, float& g) {
+        const int c = x.B.col[t];
+        g = 0.f;
+        if ((unsigned)c < (unsigned)x.B.cols) {
+            if (!look(c, g)) set_status(x.ctl, ST_INVALID);   // C lacks a product's column
+        } else {
+            set_status(x.ctl, ST_INVALID);
+        }
+    };
     double mine = 0.0;
     for (int q = 0; q < cnt; q += 4) {
-        double acc[4];
+        float acc[4];
+        double wide[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int qq = q + u;
             const int sts = __shfl_sync(kFull, ts, qq & 31);
             const int ste = qq < cnt ? __shfl_sync(kFull, te, qq & 31) : sts;
             const float sa = __shfl_sync(kFull, a, qq & 31);
-            acc[u] = 0.0;
-            for (int t = sts + lane; t < ste; t += 32) {
-                const int c = x.B.col[t];
-                float g = 0.f;
-                if ((unsigned)c < (unsigned)x.B.cols) {
-                    if (!look(c, g)) set_status(x.ctl, ST_INVALID);   // C lacks a product's column
-                } else {
-                    set_status(x.ctl, ST_INVALID);
+            acc[u] = 0.f;
+            wide[u] = 0.0;
+            if (ste - sts <= kBwdF32Len) {                      // warp-uniform
+                for (int t = sts + lane; t < ste; t += 32) {
+                    float g;
+                    lookup(t, g);
+                    acc[u] = fmaf(g, x.B.val[t], acc[u]);
+                    if (x.dB64) atomicAdd(&x.dB64[t], (double)(sa * g));
                 }
-                acc[u] += (double)g * (double)x.B.val[t];
-                if (x.dB64) atomicAdd(&x.dB64[t], (double)sa * (double)g);
+            } else {
+                for (int t = sts + lane; t < ste; t += 32) {
+                    float g;
+                    lookup(t, g);
+                    wide[u] += (double)g * (double)x.B.val[t];
+                    if (x.dB64) atomicAdd(&x.dB64[t], (double)(sa * g));
+                }
             }
         }
 #pragma unroll
@@ -88,8 +113,15 @@ __device__ __forceinline__ double bwd_chunk(const BwdArgs& x, int j0, int cnt, S
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(kFull, acc[u], o);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (lane == q + u) mine = acc[u];
+        for (int u = 0; u < 4; ++u) {
+            const int qq = q + u;
+            const bool is_wide = qq < cnt &&
+                                 __shfl_sync(kFull, te, qq & 31) - __shfl_sync(kFull, ts, qq & 31) >
+                                     kBwdF32Len;
+            double v = acc[u];
+            if (is_wide) v = warp_sum(wide[u]);                  // warp-uniform
+            if (lane == qq) mine = v;
+        }
     }
     return mine;
 }
