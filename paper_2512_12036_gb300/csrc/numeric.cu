@@ -1183,16 +1183,25 @@ __device__ __forceinline__ int auto_splits(int q, int P) {
 
 constexpr int kHotrSlots = 2048;
 constexpr int kHotrStride = kHotrSlots + 1;   // copies of one slot in different banks
-// products per warp step batch: 2 / 3 / 4 measured 254 / 248 / 268 ms on the
-// R-MAT scale 20 product (4 spills registers at the 64-register limit)
-constexpr int kHotrUnroll = 3;
+// threads per block and products per warp step batch: with 1024 threads
+// (64 registers), unroll 2 / 3 / 4 measured 254 / 248 / 268 ms on the R-MAT
+// scale 20 product (4 spills)
+#ifndef SPG_HOTR_THREADS
+#define SPG_HOTR_THREADS 1024
+#endif
+#ifndef SPG_HOTR_UNROLL
+#define SPG_HOTR_UNROLL 3
+#endif
+constexpr int kHotrThreads = SPG_HOTR_THREADS;
+constexpr int kHotrUnroll = SPG_HOTR_UNROLL;
+static_assert(kHotrThreads / kHotCopies <= 160, "a copy must gather at most 160 terms per tile");
 
-__global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hotr(
+__global__ void __launch_bounds__(kHotrThreads, 1) k_num_dense_hotr(
     CsrDev A, CsrDev B, const int* map, Ctl* ctl, const int* rptC, int row_begin, int* colC,
     float* valC, int bin_lo, int bin_hi, int tier, const int* tab, int P, int PW, int pmax,
     int cap, const int* hot_rank, const int* hot_col, const int2* bhv, const int* rc_slot,
     const unsigned* rc_bits, int rc_nslots, int rc_wpr, int splits) {
-    constexpr int kT = kHotThreads;
+    constexpr int kT = kHotrThreads;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     double* acc = reinterpret_cast<double*>(sm_raw);                  // [kHotrSlots]
     float* cp = reinterpret_cast<float*>(acc + kHotrSlots);           // [kHotCopies][kHotrStride]
@@ -1700,7 +1709,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
             const int pmax_r = p->hotr_pmax < w.panels ? p->hotr_pmax : w.panels;
             const int splits = dense_splits(p, w.panels);
             SPG_LAUNCH(p, K_NUM_DENSE64, s,
-                       k_num_dense_hotr<<<sms, kHotThreads, hotr_smem(PW, pmax_r, p->hotr_cap), s>>>(
+                       k_num_dense_hotr<<<sms, kHotrThreads, hotr_smem(PW, pmax_r, p->hotr_cap), s>>>(
                            A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
                            NB_DENSE64_0 + NB_DENSE_N, 7, w.bpanel, w.panels, PW, pmax_r,
                            p->hotr_cap, w.hot_rank, w.hot_col, w.bhv, w.rc_slot, w.rc_bits,
