@@ -8,6 +8,7 @@ namespace spg {
 void occupancy_symbolic(spgemm_plan* p);
 void occupancy_numeric(spgemm_plan* p);
 void occupancy_backward(spgemm_plan* p);
+void occupancy_mcl(spgemm_plan* p);
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long long b_cols,
@@ -104,6 +105,7 @@ void init_occupancy(spgemm_plan* p) {
     occupancy_symbolic(p);
     occupancy_numeric(p);
     occupancy_backward(p);
+    occupancy_mcl(p);
 }
 
 const char* const kKernelNames[K_NUM_KERNELS] = {

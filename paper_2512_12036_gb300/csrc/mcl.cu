@@ -5,9 +5,10 @@
 //
 // Keep/drop decisions are taken in fp32 on the value (order 0: prune and
 // top-k first, then inflate) or on the fp32-rounded inflated value (order 1:
-// inflate first). The k-th largest decision value is found by a binary
-// search over order-preserving 32-bit keys, counting with warp or block
-// reductions, so no sort is needed; kept entries keep their column order.
+// inflate first). The k-th largest decision value is found by a radix
+// selection over order-preserving 32-bit keys (four 8-bit digits, a
+// 256-bin histogram each), so no sort is needed; kept entries keep their
+// column order.
 // Weights and the row sum are fp64; each output is rounded once to fp32.
 // k < 0 keeps every entry that passes the threshold (a plain normalisation
 // when theta <= 0 and r = 1).
@@ -18,6 +19,7 @@ namespace spg {
 constexpr int kMclWarpMax = 1024;     // rows up to this length: one warp, 32 entries per lane
 constexpr int kMclThreads = 256;
 constexpr int kMclBlockThreads = 1024;
+constexpr int kMclStage = 32768;      // decision keys of a block row kept in shared memory (128 KB)
 
 struct MclParams {
     float theta;
@@ -42,6 +44,45 @@ __device__ __forceinline__ float mcl_decide(float v, const MclParams& p) {
     return p.order == 0 ? v : (float)mcl_weight(v, p.r);
 }
 
+// One radix-selection step, called by all 32 lanes of a warp: hist holds
+// the 256 bins of the current digit (keys sharing the prefix found so far),
+// `above` the keys known to be larger than that prefix. Returns in every
+// lane the digit whose bin holds the k-th largest key and the count of keys
+// above that bin. Lane l reads bins 8l .. 8l+7; a suffix sum over lanes
+// gives each lane the keys above its bins.
+__device__ __forceinline__ void mcl_radix_digit(const int* hist, int above, int k, int& dig,
+                                                int& run_at) {
+    const int lane = lane_id();
+    int c[8], tot = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        c[i] = hist[8 * lane + i];
+        tot += c[i];
+    }
+    int hi_sum = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_down_sync(kFull, hi_sum, o);
+        if (lane + o < 32) hi_sum += v;
+    }
+    int run = above + hi_sum - tot;
+    int my_dig = -1, my_run = 0;
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+        if (my_dig < 0 && run < k && run + c[i] >= k) {
+            my_dig = 8 * lane + i;
+            my_run = run;
+        }
+        run += c[i];
+    }
+    // exactly one lane's bins hold the k-th largest key
+    const unsigned who = __ballot_sync(kFull, my_dig >= 0);
+    const int src = who ? __ffs(who) - 1 : 0;
+    dig = __shfl_sync(kFull, my_dig, src);
+    run_at = __shfl_sync(kFull, my_run, src);
+    if (dig < 0) dig = 0;
+}
+
 // ---------------------------------------------------------------------------
 // One warp per row of length <= kMclWarpMax. kWrite = false: count the kept
 // entries into counts[row]; true: write them at rpt_out[row].
@@ -50,7 +91,9 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_warp(CsrDev E, MclParams pr
                                                           const int* rpt_out, int* col_out,
                                                           float* val_out, Ctl* ctl) {
     constexpr int kPer = kMclWarpMax / 32;
+    __shared__ int whist[kMclThreads / 32][256];
     const int lane = lane_id();
+    int* hist = whist[threadIdx.x >> 5];
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long row = gw; row < E.rows; row += nw) {
@@ -77,20 +120,28 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_warp(CsrDev E, MclParams pr
         unsigned K = 1u;
         int need_eq = 0;
         if (cut) {
-            unsigned lo = 1u, hi = 0xffffffffu;
-            while (lo < hi) {
-                const unsigned mid = lo + (unsigned)(((unsigned long long)hi - lo + 1ull) >> 1);
-                int c = 0;
+            // the k-th largest key by radix selection, 8 bits a pass from the
+            // top, on a per-warp 256-bin histogram (see mcl_radix_digit)
+            unsigned prefix = 0u, pmask = 0u;
+            int above = 0;
+            for (int sh = 24; sh >= 0; sh -= 8) {
 #pragma unroll
-                for (int i = 0; i < kPer; ++i) c += key[i] >= mid;
-                if (warp_sum(c) >= prm.k) lo = mid;
-                else hi = mid - 1u;
+                for (int b = 0; b < 8; ++b) hist[8 * lane + b] = 0;
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < kPer; ++i)
+                    if (key[i] != 0u && (key[i] & pmask) == prefix)
+                        atomicAdd(&hist[(key[i] >> sh) & 255u], 1);
+                __syncwarp();
+                int dig, run_at;
+                mcl_radix_digit(hist, above, prm.k, dig, run_at);
+                prefix |= (unsigned)dig << sh;
+                pmask |= 255u << sh;
+                above = run_at;
+                __syncwarp();
             }
-            K = lo;
-            int gt = 0;
-#pragma unroll
-            for (int i = 0; i < kPer; ++i) gt += key[i] > K;
-            need_eq = prm.k - warp_sum(gt);
+            K = prefix;
+            need_eq = prm.k - above;
         }
         const int keep_n = cut ? prm.k : cnt;
         if (!kWrite) {
@@ -143,7 +194,10 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_warp(CsrDev E, MclParams pr
 }
 
 // ---------------------------------------------------------------------------
-// One block per row of length > kMclWarpMax (rows taken by stride).
+// One block per row of length > kMclWarpMax (rows taken by stride). The
+// row's decision keys are computed once into shared memory (rows up to
+// kMclStage entries; longer rows recompute them per pass) and the k-th
+// largest is found by a 4-pass radix selection (8 bits a pass).
 template <bool kWrite>
 __global__ void __launch_bounds__(kMclBlockThreads) k_mcl_block(CsrDev E, MclParams prm,
                                                                 int* counts, const int* rpt_out,
@@ -152,6 +206,9 @@ __global__ void __launch_bounds__(kMclBlockThreads) k_mcl_block(CsrDev E, MclPar
     __shared__ int red[33];
     __shared__ double redd[33];
     __shared__ int scratch[33];
+    __shared__ int hist[256];
+    __shared__ int s_dig, s_above;
+    extern __shared__ unsigned skey[];             // kMclStage decision keys
     for (long long row = blockIdx.x; row < E.rows; row += gridDim.x) {
         int s, e;
         row_extent(E, (int)row, s, e, ctl);
@@ -160,25 +217,50 @@ __global__ void __launch_bounds__(kMclBlockThreads) k_mcl_block(CsrDev E, MclPar
             const float d = mcl_decide(E.val[q], prm);
             return d >= prm.theta ? ord_key(d) : 0u;
         };
+        // decision keys, staged in shared memory when the row fits
+        const int n = e - s;
+        const bool staged = n <= kMclStage;
         int c0 = 0;
-        for (int q = s + threadIdx.x; q < e; q += blockDim.x) c0 += key_of(q) != 0u;
-        const int cnt = block_sum(c0, red);
+        for (int q = s + threadIdx.x; q < e; q += blockDim.x) {
+            const unsigned kq = key_of(q);
+            if (staged) skey[q - s] = kq;
+            c0 += kq != 0u;
+        }
+        const int cnt = block_sum(c0, red);       // (barrier: skey ready)
+        auto key_at = [&](int q) -> unsigned { return staged ? skey[q - s] : key_of(q); };
         const bool cut = prm.k >= 0 && cnt > prm.k;
         unsigned K = 1u;
         int need_eq = 0;
         if (cut) {
-            unsigned lo = 1u, hi = 0xffffffffu;
-            while (lo < hi) {
-                const unsigned mid = lo + (unsigned)(((unsigned long long)hi - lo + 1ull) >> 1);
-                int c = 0;
-                for (int q = s + threadIdx.x; q < e; q += blockDim.x) c += key_of(q) >= mid;
-                if (block_sum(c, red) >= prm.k) lo = mid;
-                else hi = mid - 1u;
+            // the k-th largest key by radix selection, 8 bits a pass from the
+            // top: a 256-bin histogram of the keys that share the prefix found
+            // so far, then the digit whose bin holds the k-th largest
+            unsigned prefix = 0u, pmask = 0u;
+            int above = 0;                          // keys known to be larger than the prefix
+            for (int sh = 24; sh >= 0; sh -= 8) {
+                for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+                __syncthreads();
+                for (int q = s + threadIdx.x; q < e; q += blockDim.x) {
+                    const unsigned kq = key_at(q);
+                    if (kq != 0u && (kq & pmask) == prefix) atomicAdd(&hist[(kq >> sh) & 255u], 1);
+                }
+                __syncthreads();
+                if (threadIdx.x < 32) {
+                    int dig, run_at;
+                    mcl_radix_digit(hist, above, prm.k, dig, run_at);
+                    if (threadIdx.x == 0) {
+                        s_dig = dig;
+                        s_above = run_at;
+                    }
+                }
+                __syncthreads();
+                prefix |= (unsigned)s_dig << sh;
+                pmask |= 255u << sh;
+                above = s_above;
+                __syncthreads();
             }
-            K = lo;
-            int gt = 0;
-            for (int q = s + threadIdx.x; q < e; q += blockDim.x) gt += key_of(q) > K;
-            need_eq = prm.k - block_sum(gt, red);
+            K = prefix;
+            need_eq = prm.k - above;
         }
         const int keep_n = cut ? prm.k : cnt;
         if (!kWrite) {
@@ -231,6 +313,11 @@ __global__ void __launch_bounds__(kMclBlockThreads) k_mcl_block(CsrDev E, MclPar
     }
 }
 
+void occupancy_mcl(spgemm_plan* p) {
+    allow_max_dynamic_smem((const void*)k_mcl_block<false>, p);
+    allow_max_dynamic_smem((const void*)k_mcl_block<true>, p);
+}
+
 void launch_mcl_step(const spgemm_plan* p, const CsrDev& E, float theta, int k, double r,
                      int order, const WsPtrs& w, int* rpt_out, int* col_out, float* val_out,
                      cudaStream_t s) {
@@ -242,10 +329,10 @@ void launch_mcl_step(const spgemm_plan* p, const CsrDev& E, float theta, int k, 
     const int sms = p->num_sms;
     int* counts = w.map;                       // E.rows ints of the workspace
     SPG_LAUNCH(p, K_MCL, s, k_mcl_warp<false><<<sms * 8, kMclThreads, 0, s>>>(E, prm, counts, nullptr, nullptr, nullptr, w.ctl));
-    SPG_LAUNCH(p, K_MCL, s, k_mcl_block<false><<<sms, kMclBlockThreads, 0, s>>>(E, prm, counts, nullptr, nullptr, nullptr, w.ctl));
+    SPG_LAUNCH(p, K_MCL, s, k_mcl_block<false><<<sms, kMclBlockThreads, kMclStage * 4, s>>>(E, prm, counts, nullptr, nullptr, nullptr, w.ctl));
     launch_row_ptr(p, counts, E.rows, w, rpt_out, s);
     SPG_LAUNCH(p, K_MCL, s, k_mcl_warp<true><<<sms * 8, kMclThreads, 0, s>>>(E, prm, counts, rpt_out, col_out, val_out, w.ctl));
-    SPG_LAUNCH(p, K_MCL, s, k_mcl_block<true><<<sms, kMclBlockThreads, 0, s>>>(E, prm, counts, rpt_out, col_out, val_out, w.ctl));
+    SPG_LAUNCH(p, K_MCL, s, k_mcl_block<true><<<sms, kMclBlockThreads, kMclStage * 4, s>>>(E, prm, counts, rpt_out, col_out, val_out, w.ctl));
 }
 
 }  // namespace spg
