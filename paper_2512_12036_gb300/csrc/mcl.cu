@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_warp(CsrDev E, MclParams pr
 }
 
 // ---------------------------------------------------------------------------
-// One block per row of length > kMclWarpMax (rows taken by stride). The
+// One block per row of length > kMclWarpMax (picked from chunks of rows). The
 // row's decision keys are computed once into shared memory (rows up to
 // kMclStage entries; longer rows recompute them per pass) and the k-th
 // largest is found by a 4-pass radix selection (8 bits a pass).
@@ -209,7 +209,28 @@ __global__ void __launch_bounds__(kMclBlockThreads) k_mcl_block(CsrDev E, MclPar
     __shared__ int hist[256];
     __shared__ int s_dig, s_above;
     extern __shared__ unsigned skey[];             // kMclStage decision keys
-    for (long long row = blockIdx.x; row < E.rows; row += gridDim.x) {
+    __shared__ int s_long[kMclBlockThreads];       // this chunk's rows above kMclWarpMax
+    __shared__ int s_nlong;
+    // chunks of blockDim consecutive rows: one parallel look at their lengths
+    // picks this kernel's rows, which the block then takes one at a time
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < E.rows;
+         base += (long long)gridDim.x * blockDim.x) {
+    {
+        const long long r0 = base + threadIdx.x;
+        bool is_long = false;
+        if (r0 < E.rows) {
+            const int rs0 = E.rpt[r0], re0 = E.rpt[r0 + 1];
+            is_long = re0 - rs0 > kMclWarpMax;
+        }
+        int nl;
+        const int slot = block_excl_scan(is_long ? 1 : 0, scratch, &nl);
+        if (is_long) s_long[slot] = (int)r0;
+        if (threadIdx.x == 0) s_nlong = nl;
+        __syncthreads();
+    }
+    const int nlong = s_nlong;
+    for (int li = 0; li < nlong; ++li) {
+        const long long row = s_long[li];
         int s, e;
         row_extent(E, (int)row, s, e, ctl);
         if (e - s <= kMclWarpMax) continue;
@@ -310,6 +331,8 @@ __global__ void __launch_bounds__(kMclBlockThreads) k_mcl_block(CsrDev E, MclPar
         }
         if (threadIdx.x == 0 && pos != pend) set_status(ctl, ST_INTERNAL);
         __syncthreads();
+    }
+    __syncthreads();                               // s_long is rewritten by the next chunk
     }
 }
 
