@@ -20,6 +20,7 @@ constexpr int kMclWarpMax = 1024;     // rows up to this length: one warp, 32 en
 constexpr int kMclThreads = 256;
 constexpr int kMclBlockThreads = 1024;
 constexpr int kMclStage = 32768;      // decision keys of a block row kept in shared memory (128 KB)
+constexpr int kMclChunk = 128;        // rows the block kernel looks at together
 
 struct MclParams {
     float theta;
@@ -211,14 +212,15 @@ __global__ void __launch_bounds__(kMclBlockThreads) k_mcl_block(CsrDev E, MclPar
     extern __shared__ unsigned skey[];             // kMclStage decision keys
     __shared__ int s_long[kMclBlockThreads];       // this chunk's rows above kMclWarpMax
     __shared__ int s_nlong;
-    // chunks of blockDim consecutive rows: one parallel look at their lengths
-    // picks this kernel's rows, which the block then takes one at a time
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < E.rows;
-         base += (long long)gridDim.x * blockDim.x) {
+    // chunks of kMclChunk consecutive rows: one parallel look at their
+    // lengths picks this kernel's rows, which the block then takes one at a
+    // time (small chunks keep the blocks' shares of long rows even)
+    for (long long base = (long long)blockIdx.x * kMclChunk; base < E.rows;
+         base += (long long)gridDim.x * kMclChunk) {
     {
         const long long r0 = base + threadIdx.x;
         bool is_long = false;
-        if (r0 < E.rows) {
+        if ((int)threadIdx.x < kMclChunk && r0 < E.rows) {
             const int rs0 = E.rpt[r0], re0 = E.rpt[r0 + 1];
             is_long = re0 - rs0 > kMclWarpMax;
         }
