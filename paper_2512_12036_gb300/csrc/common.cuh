@@ -556,27 +556,17 @@ __device__ __forceinline__ void expand_walk_padded(const Off* off, const int* sb
     using Item = decltype(load(0));
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     const Off per = ((P / 32 + kWarps - 1) / kWarps) * 32;
-    const Off wbase = (Off)warp * per;
-    if (wbase >= P) return;
+    Off base = (Off)warp * per;
+    const Off wend = base + per < P ? base + per : P;
+    if (base >= wend) return;
     int lo = 0, hi = nE - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= wbase) lo = mid;
+        if (off[mid] <= base) lo = mid;
         else hi = mid - 1;
     }
-    // positions relative to the warp's first product, in 32 bits: a warp's
-    // range is at most 1/32 of a tile, and a segment starting before it is
-    // one B row (padded), below 2^31 products since B.nnz fits int32; a
-    // segment end beyond 2^31 is clamped (the range ends before it anyway)
-    const Off wlen = (wbase + per < P ? wbase + per : P) - wbase;
-    const int wend = wlen < (Off)0x7fffffc0 ? (int)wlen : 0x7fffffc0;
-    auto rel = [&](Off x) -> int {
-        const Off d = x - wbase;
-        return d > (Off)0x7fffffff ? 0x7fffffff : (d < -(Off)0x7fffffff ? -0x7fffffff : (int)d);
-    };
-    int base = 0;
     int s = lo;
-    int so = rel(off[s]), se = rel(off[s + 1]);
+    Off so = off[s], se = off[s + 1];
     int sbs = sbsv[s], sln = slnv[s];
     Acc sa = sav[s];
     while (base < wend) {
@@ -594,12 +584,12 @@ __device__ __forceinline__ void expand_walk_padded(const Off* off, const int* sb
                 if (base >= se) {                    // next segment (padded length >= 32)
                     ++s;
                     so = se;
-                    se = rel(off[s + 1]);
+                    se = off[s + 1];
                     sbs = sbsv[s];
                     sln = slnv[s];
                     sa = sav[s];
                 }
-                const int o = base - so + lane;
+                const int o = (int)(base - so) + lane;
                 tq[u] = sbs + o;
                 aq[u] = sa;
                 sq[u] = s;
@@ -623,7 +613,7 @@ __device__ __forceinline__ void expand_walk_padded(const Off* off, const int* sb
 
 template <int kT, typename Acc, int kUnroll, bool kSeg = false, class Load, class Apply>
 __device__ __forceinline__ void expand_tile_padded(ExpandTile<kT, Acc>& sm, int bs, int len, Acc a,
-                                                   Load&& load, Apply&& apply, Ctl* ctl) {
+                                                   Load&& load, Apply&& apply) {
     const int tid = threadIdx.x;
     constexpr int kWarps = kT / 32;
     constexpr unsigned long long kMask48 = (1ull << 48) - 1ull;
@@ -640,17 +630,10 @@ __device__ __forceinline__ void expand_tile_padded(ExpandTile<kT, Acc>& sm, int 
         sm.ln[ci] = len;
         sm.a[ci] = a;
     }
-    if (tid == 0) {
-        sm.off[nE] = P;
-        // the walk counts a warp's range in 32 bits: at most 2^35 products a
-        // tile (1024 A entries whose B rows average 2^25 entries); beyond
-        // that the product is refused on the status word
-        if (P >= (1ll << 35)) set_status(ctl, ST_UNSUPPORTED);
-    }
+    if (tid == 0) sm.off[nE] = P;
     __syncthreads();
-    // one walk with 64-bit segment offsets and 32-bit positions inside a
-    // warp's range (a second, all-32-bit instantiation beside a 64-bit one
-    // pushed the fp32 dense kernel past 64 registers)
+    // one 64-bit walk: a second, 32-bit instantiation here pushed the fp32
+    // dense kernel past 64 registers (spills, 16% slower)
     expand_walk_padded<long long, kWarps, Acc, kUnroll, kSeg>(sm.off, sm.bs, sm.ln, sm.a, nE, P,
                                                               load, apply);
     __syncthreads();

@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                 if (kMode == 0) {
                     // long per-pass segments: padded expansion (no segment search)
                     expand_tile_padded<kNumDenseThreads, float, kD32Unroll>(tile, bs, len, mya, load,
-                                                                           apply, ctl);
+                                                                           apply);
                 } else {
                     for (int g0 = 0; g0 < na; g0 += kGroup) {
                         const bool mine = (int)threadIdx.x >= g0 && (int)threadIdx.x < g0 + kGroup;
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                         }
                     }
                     if (kMode == 0)
-                        expand_tile_padded<kNumDenseThreads, float, 4>(tile, bs, len, a, load, apply, ctl);
+                        expand_tile_padded<kNumDenseThreads, float, 4>(tile, bs, len, a, load, apply);
                     else
                         expand_tile<kNumDenseThreads, float, 4>(tile, bs, len, a, load, apply);
                     if (kMode == 1) flush();
@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                 for (int i = t; i < nw; i += kT) bm[i] = src[i];
                 __syncthreads();
             } else {
-                expand_tile_padded<kT, float, kRankOccUnroll>(tile, bs, len, mya, load_key, mark, ctl);
+                expand_tile_padded<kT, float, kRankOccUnroll>(tile, bs, len, mya, load_key, mark);
             }
             // 2. word ranks and the pass's columns (thread t owns words [wb, wb + wpt))
             const int wpt = (nw + kT - 1) / kT;
@@ -871,7 +871,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                 hi = s_hi;
                 rbase = rk[lo];
                 const int cnt_sub = (hi < nw ? rk[hi] : tot) - rbase;
-                expand_tile_padded<kT, float, kD32Unroll>(tile, bs, len, mya, load, add, ctl);
+                expand_tile_padded<kT, float, kD32Unroll>(tile, bs, len, mya, load, add);
                 for (int i = t; i < cnt_sub; i += kT) {
                     const int o = written + rbase + i;
                     if (o < nnz_row) valC[out + o] = vals[i];
