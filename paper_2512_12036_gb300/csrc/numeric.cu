@@ -46,21 +46,6 @@ struct KeyVal {
     float v;
 };
 
-// L1 prefetch of a B record `ahead` positions further along the walk (the
-// same lane's position one unrolled batch later when the segment goes on);
-// clamped inside the array, takes no register for the data.
-__device__ __forceinline__ void prefetch_l1(const int2* base, long long q, long long n) {
-#ifdef SPG_PREFETCH_AHEAD
-    long long p = q + SPG_PREFETCH_AHEAD;
-    if (p >= n) p = n - 1;
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(base + p));
-#else
-    (void)base;
-    (void)q;
-    (void)n;
-#endif
-}
-
 __device__ __forceinline__ bool key_in(int key, const CsrDev& B, Ctl* ctl) {
     if ((unsigned)key >= (unsigned)B.cols) {
         set_status(ctl, ST_INVALID);
@@ -759,7 +744,6 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
         else if (key_in(key, B, ctl)) set_status(ctl, ST_INTERNAL);
     };
     auto load = [&](int q) {
-        prefetch_l1(bcv, q, B.nnz);
         const int2 v = bcv[q];
         return KeyVal{v.x, __int_as_float(v.y)};
     };
@@ -1246,7 +1230,6 @@ __global__ void __launch_bounds__(kHotrThreads, 1) k_num_dense_hotr(
     int c0 = 0, span = 0, hr0 = 0, nhs = 0, hrp0 = 0, hrp1 = 0;
     bool cold = true;
     auto load = [&](int q) {
-        prefetch_l1(bhv, q, B.nnz);
         const int2 v = bhv[q];
         return KeyVal{v.x, __int_as_float(v.y)};
     };
