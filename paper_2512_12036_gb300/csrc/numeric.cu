@@ -1255,16 +1255,29 @@ __global__ void __launch_bounds__(kHotrThreads, 1) k_num_dense_hotr(
             set_status(ctl, ST_INTERNAL);                                      // outside the pass
         }
     };
+    // the copies of this walk's slots into the slot sums. With the copies
+    // (split), a slot sum is a double-float pair (hi, lo) in the slot's 8
+    // bytes, each copy added exactly by Knuth's TwoSum (the rounding error of
+    // hi + x recovered in fp32 and carried in lo): fp32 work only, since
+    // GB300's fp64 pipe runs at 1/64 of its fp32 rate; the pair holds the sum
+    // to about 2^-44 of its terms' magnitude, far inside the bound. Without
+    // the copies the products went straight into an fp64 sum (acc).
+    float2* acc2 = reinterpret_cast<float2*>(acc);
     auto fold = [&]() {
         if (split) {
             for (int h = t; h < nhs; h += kT) {
-                double v = acc[h];
+                float2 v = acc2[h];
 #pragma unroll
                 for (int c = 0; c < kHotCopies; ++c) {
-                    v += (double)cp[c * kHotrStride + h];
+                    const float x = cp[c * kHotrStride + h];
                     cp[c * kHotrStride + h] = 0.f;
+                    const float sum = v.x + x;
+                    const float bp = sum - v.x;
+                    const float err = (v.x - (sum - bp)) + (x - bp);
+                    v.x = sum;
+                    v.y += err;
                 }
-                acc[h] = v;
+                acc2[h] = v;
             }
         }
         __syncthreads();
@@ -1433,14 +1446,21 @@ __global__ void __launch_bounds__(kHotrThreads, 1) k_num_dense_hotr(
                 // round the slot range's sums once into the value array
                 for (int h = t; h < nhs; h += kT) {
                     const int kk = hot_col[hr0 + h] - c0;
-                    const double v = acc[h];
-                    acc[h] = 0.0;
+                    float v;
+                    if (split) {
+                        const float2 p2 = acc2[h];
+                        v = p2.x + p2.y;                 // one rounding of the pair
+                        acc2[h] = make_float2(0.f, 0.f);
+                    } else {
+                        v = (float)acc[h];
+                        acc[h] = 0.0;
+                    }
                     if ((unsigned)kk < (unsigned)span) {
                         const unsigned word = bm[kk >> 5];
                         const int rr = rk[kk >> 5] + __popc(word & ((1u << (kk & 31)) - 1u));
                         if (((word >> (kk & 31)) & 1u) && (unsigned)rr < (unsigned)cap)
-                            vals[rr] = (float)v;
-                        else if (v != 0.0)
+                            vals[rr] = v;
+                        else if (v != 0.f)
                             set_status(ctl, ST_INTERNAL);
                     } else {
                         set_status(ctl, ST_INTERNAL);

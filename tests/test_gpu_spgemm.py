@@ -138,11 +138,15 @@ def test_dense_tier_repeated_columns_in_b(plan):
     check_product(plan, A, B)
 
 
-def test_dense_tier_small_terms_after_large(plan):
+@pytest.mark.parametrize("cache", [0, 16])
+def test_dense_tier_small_terms_after_large(plan, cache):
     # one row of 1024 ones against B rows that all hold column 0 (a hot
     # column): B[0,0] = 1 and B[k,0] = 2^-25 for k > 0. A single fp32 running
     # sum that takes the 1 first loses every small term (3e-5 of the sum);
-    # the tier's partial sums must stay within the 1e-5 bound
+    # the tier's partial sums must stay within the 1e-5 bound (cache: the
+    # rank-compacted fp64 tier, whose slot sums are double-float pairs)
+    if cache:
+        plan = Plan(row_cache_mb=cache)
     rng = np.random.default_rng(41)
     na, cols = 1024, 40000
     r, c, v = [], [], []
