@@ -900,10 +900,12 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
 // gathers at most kHotThreads / kHotCopies = 128 terms per column. A
 // product reads B's column word (the column, or sign bit | hot rank for a
 // hot column) beside its value. After every tile
-// the copies are added into an fp64 accumulator in a fixed order and
-// cleared; at the end of the sub-pass the accumulator is rounded once into
-// the pass array. The error stays within (gamma_128 + u) * sum|a||b| plus
-// fp64 rounding, below the 1e-5 bound, with fp32 shared-memory atomics only.
+// the copies are added, in a fixed order, into a double-float sum per slot
+// (an fp32 pair kept exact by TwoSum) and cleared; at the end of the
+// sub-pass the pair is rounded once into the pass array. The error stays
+// within (gamma_128 + u) * sum|a||b| plus the pair's ~2^-44 relative
+// rounding, below the 1e-5 bound, with fp32 arithmetic and shared-memory
+// atomics only.
 // When B has unsorted or repeated columns (ctl->b_unsorted != 0) the bound
 // does not hold and hot-column products go straight to the fp64
 // accumulator with fp64 atomics instead.
@@ -992,16 +994,27 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
         if (hot && !split) atomicAdd(&acc[x], (double)a * (double)kv.v);
         else atomicAdd(hot ? &cp[(seg & (kHotCopies - 1)) * kHotSlots + x] : &st[x], a * kv.v);
     };
-    // add the copies of this sub-pass's hot slots into the fp64 accumulator
+    // add the copies of this sub-pass's hot slots into the slot sums: with
+    // the copies (split) a double-float pair per slot, each copy added by
+    // TwoSum in fp32 (GB300's fp64 pipe is slow; see k_num_dense_hotr);
+    // without them the products went straight into the fp64 sum (acc)
+    float2* acc2 = reinterpret_cast<float2*>(acc);
     auto fold = [&]() {
-        for (int h = t; h < nhs; h += kHotThreads) {
-            double v = acc[h];
+        if (split) {
+            for (int h = t; h < nhs; h += kHotThreads) {
+                float2 v = acc2[h];
 #pragma unroll
-            for (int c = 0; c < kHotCopies; ++c) {
-                v += (double)cp[c * kHotSlots + h];
-                cp[c * kHotSlots + h] = 0.f;
+                for (int c = 0; c < kHotCopies; ++c) {
+                    const float x = cp[c * kHotSlots + h];
+                    cp[c * kHotSlots + h] = 0.f;
+                    const float sum = v.x + x;
+                    const float bp = sum - v.x;
+                    const float err = (v.x - (sum - bp)) + (x - bp);
+                    v.x = sum;
+                    v.y += err;
+                }
+                acc2[h] = v;
             }
-            acc[h] = v;
         }
         __syncthreads();
     };
@@ -1122,7 +1135,7 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
                 for (int h = t; h < nhs; h += kHotThreads) {
                     const int kk = hot_col[hr0 + h] - pc0;
                     if ((unsigned)kk < (unsigned)W) {
-                        st[kk] = (float)acc[h];
+                        st[kk] = split ? acc2[h].x + acc2[h].y : (float)acc[h];
                         if (cbits == nullptr && ((touched[h >> 5] >> (h & 31)) & 1u))
                             atomicOr(&bm[kk >> 5], 1u << (kk & 31));
                     }
