@@ -202,7 +202,12 @@ class ClockSampler:
 # full case; the summary and its command are kept under profiles/).
 # Scaled by the full workload's products of the tier to give the per-launch
 # traffic; a kernel changed since its capture must drop out of this table.
-DRAM_BYTES_PER_PRODUCT = {"num_dense64": (493.987072e6 + 335.559e6) / 256228740}
+DRAM_BYTES_PER_PRODUCT = {
+    # k_num_dense_hotr (rank-compacted fp64-bound tier with the row bitmap cache)
+    "num_dense64": (987.079168e6 + 346.908928e6) / 256228740,
+    # k_num_dense_rank (rank-compacted fp32 tier with the row bitmap cache)
+    "num_dense32": (1100.085e6 + 1083.108e6) / 257686006,
+}
 
 
 def max_over_ranks(x: float, device) -> float:
