@@ -5,7 +5,8 @@
 // fp32 (fused multiply-add, the same arithmetic as the rest of the layer)
 // as register-tiled GEMMs:
 //   a 128 x 128 output tile per block of 256 threads, 8 x 8 outputs per
-//   thread, k-steps of 16 staged through shared memory in two buffers (the
+//   thread (rows ty*8.., columns tx*4.. and 64+tx*4..), k-steps of 16
+//   staged through shared memory in two buffers (the
 //   next step's tile is fetched into registers while the current one is
 //   multiplied). Either operand may be read transposed. A long reduction
 //   (dW sums over every row of the graph) is split over blocks along K:
@@ -100,8 +101,10 @@ __global__ void __launch_bounds__(kGemmThreads, 2)
         for (int k = 0; k < kGemmBK; ++k) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8]);
             const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 8 + 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 8]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 8 + 4]);
+            // columns tx*4 .. +3 and 64 + tx*4 .. +3: a warp's 16 column
+            // groups read 256 contiguous bytes per load (two wavefronts)
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + tx * 4]);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2)
         if (m >= M) continue;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int n = n0 + tx * 8 + j;
+            const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
             if (n >= N) continue;
             if (Cacc) atomicAdd(&Cacc[(long long)m * N + n], (double)acc[i][j]);
             else C[(long long)m * ldc + n] = acc[i][j];
