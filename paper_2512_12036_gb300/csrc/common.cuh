@@ -159,6 +159,45 @@ __device__ __forceinline__ T block_sum(T v, T* scratch) {
     return r;
 }
 
+// One radix-selection step, called by all 32 lanes of a warp: hist holds
+// the 256 bins of the current digit (keys sharing the prefix found so far),
+// `above` the keys known to be larger than that prefix. Returns in every
+// lane the digit whose bin holds the k-th largest key and the count of keys
+// above that bin. Lane l reads bins 8l .. 8l+7; a suffix sum over lanes
+// gives each lane the keys above its bins.
+__device__ __forceinline__ void radix_digit256(const int* hist, int above, int k, int& dig,
+                                                int& run_at) {
+    const int lane = lane_id();
+    int c[8], tot = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        c[i] = hist[8 * lane + i];
+        tot += c[i];
+    }
+    int hi_sum = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_down_sync(kFull, hi_sum, o);
+        if (lane + o < 32) hi_sum += v;
+    }
+    int run = above + hi_sum - tot;
+    int my_dig = -1, my_run = 0;
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+        if (my_dig < 0 && run < k && run + c[i] >= k) {
+            my_dig = 8 * lane + i;
+            my_run = run;
+        }
+        run += c[i];
+    }
+    // exactly one lane's bins hold the k-th largest key
+    const unsigned who = __ballot_sync(kFull, my_dig >= 0);
+    const int src = who ? __ffs(who) - 1 : 0;
+    dig = __shfl_sync(kFull, my_dig, src);
+    run_at = __shfl_sync(kFull, my_run, src);
+    if (dig < 0) dig = 0;
+}
+
 // Operand views passed by value to kernels.
 struct CsrDev {
     int rows, cols;

@@ -6,8 +6,9 @@
 //     mask M_k and the kept values). Order: fp32 values compared through an
 //     order-preserving 32-bit key (IEEE total order: -NaN < -inf < ... <
 //     +inf < +NaN); equal keys go to the smaller column. The k-th largest
-//     key is found by a bitwise binary search with warp/block counts, so no
-//     sort is needed.
+//     key is found by a radix selection (one warp per row: four 8-bit digits
+//     on a 256-bin histogram) or a bitwise binary search with block counts
+//     (rows longer than a warp holds), so no sort is needed.
 //   scatter: a CSR matrix added into a dense matrix (M_k (.) G of Eq. 3 when
 //     the values are a gradient on the mask's pattern).
 //   gather: a dense matrix read at a CSR pattern (the gradient of A*TopK(X)
@@ -26,10 +27,13 @@ __device__ __forceinline__ unsigned topk_key(float x) {
 }
 
 // One warp per row (d <= kTopkWarpMax).
+// kPer: 32-column groups a lane holds (rows of up to 32 * kPer columns).
+template <int kPer>
 __global__ void __launch_bounds__(kTopkThreads) k_topk_warp(const float* X, int n, int d,
                                                             long long ldx, int k, int* rpt,
                                                             int* col, float* val) {
-    constexpr int kPer = kTopkWarpMax / 32;
+    __shared__ int whist[kTopkThreads / 32][256];
+    int* hist = whist[threadIdx.x >> 5];
     const int lane = lane_id();
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -42,30 +46,46 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk_warp(const float* X, int 
             const int c = lane + 32 * i;
             key[i] = c < d ? topk_key(x[c]) : 0u;   // columns past d are never counted
         }
-        // largest K with #(real keys >= K) >= kk (K = 0 always qualifies)
+        // (the loops below stop at the row's last 32-column group: d is
+        // uniform, so the unrolled groups past it are skipped by the warp)
+        // K = the kk-th largest key (the largest K with #(keys >= K) >= kk),
+        // by radix selection: 8 bits a pass from the top, a per-warp 256-bin
+        // histogram of the keys sharing the prefix found so far
         unsigned K = 0u;
         int need_eq = kk;
-        if (kk < d) {
-            unsigned lo = 0u, hi = 0xffffffffu;
-            while (lo < hi) {
-                const unsigned mid = lo + (unsigned)(((unsigned long long)hi - lo + 1ull) >> 1);
-                int c = 0;
+        if (kk == 0) {
+            K = 0xffffffffu;                         // nothing kept
+            need_eq = 0;
+        } else if (kk < d) {
+            unsigned prefix = 0u, pmask = 0u;
+            int above = 0;
+            for (int sh = 24; sh >= 0; sh -= 8) {
 #pragma unroll
-                for (int i = 0; i < kPer; ++i) c += (lane + 32 * i < d) && key[i] >= mid;
-                if (warp_sum(c) >= kk) lo = mid;
-                else hi = mid - 1u;
+                for (int b = 0; b < 8; ++b) hist[8 * lane + b] = 0;
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) {
+                    if (32 * i >= d) break;                         // warp-uniform
+                    if (lane + 32 * i < d && (key[i] & pmask) == prefix)
+                        atomicAdd(&hist[(key[i] >> sh) & 255u], 1);
+                }
+                __syncwarp();
+                int dig, run_at;
+                radix_digit256(hist, above, kk, dig, run_at);
+                prefix |= (unsigned)dig << sh;
+                pmask |= 255u << sh;
+                above = run_at;
+                __syncwarp();
             }
-            K = lo;
-            int gt = 0;
-#pragma unroll
-            for (int i = 0; i < kPer; ++i) gt += (lane + 32 * i < d) && key[i] > K;
-            need_eq = kk - warp_sum(gt);
+            K = prefix;
+            need_eq = kk - above;
         }
         // write kept entries in column order (column 32*i + lane)
         const long long base = row * (long long)kk;
         int pos = 0, eq_seen = 0;
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
+            if (32 * i >= d) break;                                 // warp-uniform
             const int c = lane + 32 * i;
             bool keep;
             if (kk == d) {
@@ -185,7 +205,8 @@ void launch_topk(const spgemm_plan* p, const float* X, int n, int d, long long l
         if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
         if (blocks < 1) blocks = 1;
         SPG_LAUNCH(p, K_LAYER, s,
-                   k_topk_warp<<<(int)blocks, kTopkThreads, 0, s>>>(X, n, d, ldx, k, rpt, col, val));
+                   (d <= 256 ? k_topk_warp<8> : k_topk_warp<kTopkWarpMax / 32>)<<<(int)blocks, kTopkThreads, 0, s>>>(
+                       X, n, d, ldx, k, rpt, col, val));
     } else {
         const int blocks = n < sms * 2 ? (n > 0 ? n : 1) : sms * 2;
         SPG_LAUNCH(p, K_LAYER, s,
