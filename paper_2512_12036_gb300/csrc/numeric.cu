@@ -705,6 +705,10 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
 // accumulated in word ranges of at most `cap` entries.
 constexpr int kRankPanels = 24;       // 8 and 16 measured slower, 32 leaves too few values
 constexpr int kRankOccUnroll = 8;     // occupancy expansion items are one int
+// bitmap words a thread holds in registers per pass: kRankPanels panels of
+// at most 16384 columns over kD32Threads threads
+constexpr int kRankWpt = 12;
+static_assert(kRankPanels * (16384 / 32) <= kRankWpt * kD32Threads, "pass words per thread");
 
 // With a row bitmap cache, a row that holds a slot reads each pass's bitmap
 // words from it (one coalesced copy) instead of the occupancy expansion.
@@ -732,6 +736,10 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
     if (begin >= end) return;
     if (tab == nullptr || (ctl->b_unsorted & 1) != 0) return;     // fallback kernel's rows
     const int t = threadIdx.x;
+    if (RW > kRankWpt * kT) {                         // panels wider than the options allow
+        if (t == 0) set_status(ctl, ST_INTERNAL);
+        return;
+    }
     for (int i = t; i < RW; i += kT) bm[i] = 0u;
     for (int i = t; i < cap; i += kT) vals[i] = 0.f;
     const long long stride = P + 1;
@@ -765,12 +773,19 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
         else set_status(ctl, ST_INTERNAL);
     };
 
+    // thread 0 fetches the next row one row ahead (the pending atomic stays
+    // in a register until the next row starts), so its latency hides behind
+    // the current row
+    int nxt_idx = 0;
+    if (t == 0) nxt_idx = begin + atomicAdd(&ctl->work[tier], 1);
+    bool dirty = false;              // bm holds words of an earlier pass
     for (;;) {
-        if (t == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
+        if (t == 0) s_idx = nxt_idx;
         __syncthreads();
         const int idx = s_idx;
         __syncthreads();
         if (idx >= end) break;
+        if (t == 0) nxt_idx = begin + atomicAdd(&ctl->work[tier], 1);
         const int r = map[idx];
         const int row = row_begin + r;
         const int out = rptC[r];
@@ -821,28 +836,47 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                     len = nxt - cur;
                 }
             }
-            // 1. occupancy (c0 is a multiple of the panel width, so of 32)
+            // 1. occupancy (c0 is a multiple of the panel width, so of 32):
+            // thread t holds words [wb, wb + wpt) of the pass in registers,
+            // loaded from the cached bitmap or read after the marks
             const int nw = (span + 31) >> 5;
-            if (cbits != nullptr) {
-                const unsigned* src = cbits + (c0 >> 5);
-                for (int i = t; i < nw; i += kT) bm[i] = src[i];
-                __syncthreads();
-            } else {
-                expand_tile_padded<kT, float, kRankOccUnroll>(tile, bs, len, mya, load_key, mark);
-            }
-            // 2. word ranks and the pass's columns (thread t owns words [wb, wb + wpt))
             const int wpt = (nw + kT - 1) / kT;
             const int wb = t * wpt;
             int cnt = 0;
-            for (int q = 0; q < wpt; ++q)
-                if (wb + q < nw) cnt += __popc(bm[wb + q]);
+            if (cbits != nullptr) {
+                const unsigned* src = cbits + (c0 >> 5);
+                for (int q = 0; q < wpt; ++q)
+                    if (wb + q < nw) {
+                        const unsigned v = src[wb + q];
+                        bm[wb + q] = v;
+                        cnt += __popc(v);
+                    }
+            } else {
+                if (dirty) {                          // marks need a clear bitmap
+                    for (int i = t; i < nw; i += kT) bm[i] = 0u;
+                    __syncthreads();
+                }
+                expand_tile_padded<kT, float, kRankOccUnroll>(tile, bs, len, mya, load_key, mark);
+                for (int q = 0; q < wpt; ++q)
+                    if (wb + q < nw) cnt += __popc(bm[wb + q]);
+            }
+            dirty = true;
+            // 2. word ranks, and the columns of ranks below cap staged at
+            // their ranks in the value array (stored to C coalesced below);
+            // a thread reads back only the words it wrote
             int tot;
             int run = block_excl_scan(cnt, scratch, &tot);
+            int* stage = reinterpret_cast<int*>(vals);
             for (int q = 0; q < wpt; ++q) {
                 const int w = wb + q;
                 if (w >= nw) break;
                 rk[w] = run;
-                run += __popc(bm[w]);
+                unsigned bits = bm[w];
+                while (bits) {
+                    if ((unsigned)run < (unsigned)cap) stage[run] = c0 + w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    ++run;
+                }
             }
             __syncthreads();
             // 3. values, in word ranges of at most cap entries
@@ -867,11 +901,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                 hi = s_hi;
                 rbase = rk[lo];
                 const int cnt_sub = (hi < nw ? rk[hi] : tot) - rbase;
-                // the range's columns: each thread writes its words' columns
-                // into the value array at their ranks, then the block stores
-                // them to C coalesced and clears the array for the values
-                {
-                    int* stage = reinterpret_cast<int*>(vals);
+                if (lo > 0) {                         // a later range: stage its columns now
                     for (int q = 0; q < wpt; ++q) {
                         const int w = wb + q;
                         if (w >= hi) break;
@@ -885,12 +915,15 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                         }
                     }
                     __syncthreads();
-                    for (int i = t; i < cnt_sub; i += kT) {
-                        const int o = written + rbase + i;
-                        if (o < nnz_row) colC[out + o] = stage[i];
-                        vals[i] = 0.f;
-                    }
-                    // (the expansion's block scan orders the clears before any add)
+                }
+                // the range's columns to C, coalesced; every staged slot is
+                // cleared for the values (the expansion's block scan orders
+                // the clears before any add)
+                const int ncl = lo == 0 ? (tot < cap ? tot : cap) : cnt_sub;
+                for (int i = t; i < ncl; i += kT) {
+                    const int o = written + rbase + i;
+                    if (i < cnt_sub && o < nnz_row) colC[out + o] = stage[i];
+                    vals[i] = 0.f;
                 }
                 expand_tile_padded<kT, float, kD32Unroll>(tile, bs, len, mya, load, add);
                 for (int i = t; i < cnt_sub; i += kT) {
@@ -900,10 +933,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                 }
                 __syncthreads();
             }
-            for (int q = 0; q < wpt; ++q)
-                if (wb + q < nw) bm[wb + q] = 0u;
             written += tot;
-            __syncthreads();
             cur = nxt;
             nxt = nxt2;
         }
