@@ -372,6 +372,15 @@ __global__ void __launch_bounds__(kNarrowMaxWarps * 32) k_sym_narrow(CsrDev A, C
 
 // ---------------------------------------------------------------------------
 
+// table of the block tier's two lighter bins: their rows hold at most
+// 2^(Lmax - 2) products (Lmax = log2 of block_max_ip, rounded up), so at most
+// that many distinct columns, at most half of 2^(Lmax - 1) slots
+static size_t sym_block_small_smem(const spgemm_plan* p) {
+    const int Lmax = log2_ceil_ll(p->opts.block_max_ip);
+    const int bits = Lmax - 1 > 6 ? Lmax - 1 : 6;
+    return (size_t)4 << bits;
+}
+
 static size_t sym_dense_smem(const spgemm_plan* p) {
     size_t words = kSymDenseWords;
     const size_t stat = sizeof(ExpandTile<kSymDenseThreads, float>) + 1024;
@@ -397,6 +406,9 @@ void occupancy_symbolic(spgemm_plan* p) {
                                                   kWarpsPerBlockSW * 32, sw);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block, k_sym_block,
                                                   kSymBlockThreads, sb);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block_small, k_sym_block,
+                                                  kSymBlockThreads, sym_block_small_smem(p));
+    if (p->occ_sym_block_small < 1) p->occ_sym_block_small = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_dense, k_sym_dense,
                                                   kSymDenseThreads, sd);
     if (p->occ_sym_warp < 1) p->occ_sym_warp = 1;
@@ -440,10 +452,23 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
                 break;
             }
     }
+    // bins SB_BLOCK0 and +1 with the full table (one block per SM), the two
+    // lighter bins (IP at most a quarter of block_max_ip) with a quarter-size
+    // table and several blocks per SM
+    const int split = staged_lo < SB_BLOCK0 + 2 ? staged_lo : SB_BLOCK0 + 2;
     SPG_LAUNCH(p, K_SYM_BLOCK, s,
                k_sym_block<<<sms * p->occ_sym_block, kSymBlockThreads, (size_t)tb * 4, s>>>(
-                   A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, staged_lo, 0, max_bits,
+                   A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, split, 0, max_bits,
                    hash_load(p)));
+    if (split < staged_lo) {
+        const size_t ss = sym_block_small_smem(p);
+        int small_bits = 0;
+        while (((size_t)4 << small_bits) < ss) ++small_bits;
+        SPG_LAUNCH(p, K_SYM_BLOCK, s,
+                   k_sym_block<<<sms * p->occ_sym_block_small, kSymBlockThreads, ss, s>>>(
+                       A, B, ip, w.map, w.ctl, row_nnz, split, staged_lo, 3, small_bits,
+                       hash_load(p)));
+    }
     if (staged_lo < SB_BLOCK0 + SB_BLOCK_N)
         SPG_LAUNCH(p, K_SYM_BLOCK, s,
                    k_sym_block_staged<<<sms * p->occ_sym_staged, kStageThreads, staged_smem(), s>>>(
