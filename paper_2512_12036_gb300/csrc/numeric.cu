@@ -686,6 +686,38 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
     }
 }
 
+// Word ranks and columns of a thread's bitmap words [wb, wb + wpt) of a pass
+// (run: the rank of its first entry; every rank below the value array's
+// size). Two words per step, so the two bit-extraction chains interleave
+// (fp32 dense tier 212 -> 208 ms; no gain in the fp64-bound tier).
+__device__ __forceinline__ void stage_pairs(const unsigned* bm, int* rk, int* stage, int wb,
+                                            int wpt, int nw, int run, int c0) {
+    for (int q = 0; q < wpt; q += 2) {
+        const int w = wb + q;
+        if (w >= nw) break;
+        const bool two = q + 1 < wpt && w + 1 < nw;
+        unsigned x = bm[w];
+        unsigned y = two ? bm[w + 1] : 0u;
+        rk[w] = run;
+        int rx = run;
+        run += __popc(x);
+        if (two) rk[w + 1] = run;
+        int ry = run;
+        run += __popc(y);
+        const int cx = c0 + w * 32, cy = cx + 32;
+        while (x | y) {
+            if (x) {
+                stage[rx++] = cx + __ffs(x) - 1;
+                x &= x - 1;
+            }
+            if (y) {
+                stage[ry++] = cy + __ffs(y) - 1;
+                y &= y - 1;
+            }
+        }
+    }
+}
+
 // fp32 dense tier with rank-compacted passes (rows whose A entries fit the
 // block and whose B rows are sorted; k_num_dense<0> takes the others). A
 // pass covers up to kRankPanels table panels; the row's occupancy is
@@ -867,15 +899,19 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
             int tot;
             int run = block_excl_scan(cnt, scratch, &tot);
             int* stage = reinterpret_cast<int*>(vals);
-            for (int q = 0; q < wpt; ++q) {
-                const int w = wb + q;
-                if (w >= nw) break;
-                rk[w] = run;
-                unsigned bits = bm[w];
-                while (bits) {
-                    if ((unsigned)run < (unsigned)cap) stage[run] = c0 + w * 32 + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    ++run;
+            if (tot <= cap) {
+                stage_pairs(bm, rk, stage, wb, wpt, nw, run, c0);
+            } else {                                  // ranks past cap staged per range below
+                for (int q = 0; q < wpt; ++q) {
+                    const int w = wb + q;
+                    if (w >= nw) break;
+                    rk[w] = run;
+                    unsigned bits = bm[w];
+                    while (bits) {
+                        if ((unsigned)run < (unsigned)cap) stage[run] = c0 + w * 32 + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        ++run;
+                    }
                 }
             }
             __syncthreads();
