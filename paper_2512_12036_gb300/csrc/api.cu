@@ -50,17 +50,23 @@ WsLayout ws_layout(const spgemm_plan* p, long long m, long long b_rows, long lon
     const long long wpr = (b_cols + 31) / 32;
     if (p->opts.row_cache_mb > 0 && m > 0 && wpr > 0 && wpr <= kRowCacheMaxWords) {
         const size_t bytes = (size_t)p->opts.row_cache_mb << 20;
-        const size_t slot_bytes = align256(sizeof(int) * (size_t)m);
-        const size_t row_bytes = sizeof(unsigned) * (size_t)wpr;
+        // per slot: the bitmap, and the entry count of each table panel
+        const bool counts = L.panels > 0 && L.panels <= kMaxPanels;
+        const size_t slot_bytes = align256(sizeof(int) * (size_t)m) + (counts ? 256 : 0);
+        const size_t row_bytes = sizeof(unsigned) * (size_t)wpr + (counts ? sizeof(int) * (size_t)L.panels : 0);
         long long n = bytes > slot_bytes ? (long long)((bytes - slot_bytes) / row_bytes) : 0;
         if (n > m) n = m;
         if (n > 0) {
             L.rc_nslots = (int)n;
             L.rc_wpr = (int)wpr;
             L.rc_slot = off;
-            off += slot_bytes;
+            off += align256(sizeof(int) * (size_t)m);
             L.rc_bits = off;
-            off = align256(off + row_bytes * (size_t)n);
+            off = align256(off + sizeof(unsigned) * (size_t)wpr * (size_t)n);
+            if (counts) {
+                L.rc_pc = off;
+                off = align256(off + sizeof(int) * (size_t)L.panels * (size_t)n);
+            }
         }
     }
     L.total = off;
@@ -84,6 +90,7 @@ WsPtrs ws_ptrs(const WsLayout& L, void* ws, int panel_cols) {
     w.bcv = L.has_hot ? (int2*)(b + L.bcv) : nullptr;
     w.rc_slot = L.rc_nslots > 0 ? (int*)(b + L.rc_slot) : nullptr;
     w.rc_bits = L.rc_nslots > 0 ? (unsigned*)(b + L.rc_bits) : nullptr;
+    w.rc_pc = L.rc_nslots > 0 && L.rc_pc > 0 ? (int*)(b + L.rc_pc) : nullptr;
     w.rc_nslots = L.rc_nslots;
     w.rc_wpr = L.rc_wpr;
     w.nblk = L.nblk;

@@ -121,6 +121,7 @@ struct WsLayout {
     size_t bcv = 0;          // int2 [B.nnz]      (column, value bits) per B entry, packed per call
     size_t rc_slot = 0;      // int32 [m]         row -> bitmap slot (-1: none)
     size_t rc_bits = 0;      // u32 [rc_nslots][rc_wpr] row bitmaps of the allocation phase
+    size_t rc_pc = 0;        // int [rc_nslots][panels] entries of each table panel of a cached row
     int rc_nslots = 0, rc_wpr = 0;
     bool has_hot = false;
     size_t total = 0;
@@ -144,6 +145,7 @@ struct WsPtrs {
     int2* bcv;
     int* rc_slot;            // nullptr: no row bitmap cache
     unsigned* rc_bits;
+    int* rc_pc;              // per-panel entry counts of the cached rows, or nullptr
     int rc_nslots, rc_wpr;
     int nblk, nscan, panels, panel_cols;
 };

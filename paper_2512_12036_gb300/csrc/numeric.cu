@@ -1301,7 +1301,7 @@ __global__ void __launch_bounds__(kHotrThreads, 1) k_num_dense_hotr(
     CsrDev A, CsrDev B, const int* map, Ctl* ctl, const int* rptC, int row_begin, int* colC,
     float* valC, int bin_lo, int bin_hi, int tier, const int* tab, int P, int PW, int pmax,
     int cap, const int* hot_rank, const int* hot_col, const int2* bhv, const int* rc_slot,
-    const unsigned* rc_bits, int rc_nslots, int rc_wpr, int splits) {
+    const unsigned* rc_bits, const int* rc_pc, int rc_nslots, int rc_wpr, int splits) {
     constexpr int kT = kHotrThreads;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     double* acc = reinterpret_cast<double*>(sm_raw);                  // [kHotrSlots]
@@ -1316,14 +1316,13 @@ __global__ void __launch_bounds__(kHotrThreads, 1) k_num_dense_hotr(
     __shared__ ExpandTile<kT, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
     if (begin >= end) return;
-    if (tab == nullptr || (ctl->b_unsorted & 1) != 0 || rc_slot == nullptr) return;
-    const int t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    if (tab == nullptr || (ctl->b_unsorted & 1) != 0 || rc_slot == nullptr || rc_pc == nullptr) return;
+    const int t = threadIdx.x;
     for (int i = t; i < kHotrSlots; i += kT) acc[i] = 0.0;
     for (int i = t; i < kHotCopies * kHotrStride; i += kT) cp[i] = 0.f;
     for (int i = t; i < cap; i += kT) vals[i] = 0.f;
     const bool split = ctl->b_unsorted == 0;       // copies bound the terms per column
     const long long stride = P + 1;
-    const int wpp = PW >> 5;                       // bitmap words per table panel
 
     // pass start c0 and width span, hot ranks of this walk [hr0, hr0 + nhs),
     // of the pass [hrp0, hrp1); cold: this walk adds cold products
@@ -1421,26 +1420,23 @@ __global__ void __launch_bounds__(kHotrThreads, 1) k_num_dense_hotr(
         row_extent(A, row, rs, re, ctl);
         const int na = re - rs;
         const bool cached = na <= kT;
-        // entries per panel (popcounts of the cached bitmap) and hot columns
-        // per panel for this item's panels; entries before them = its offset
+        // entries per panel (counted by the allocation phase beside the
+        // cached bitmap) and hot columns per panel for this item's panels;
+        // entries before them = its offset
         int before = 0;
-        for (int p = warp; p < gp1; p += kT / 32) {
-            const int w0 = p * wpp, w1 = w0 + wpp < rc_wpr ? w0 + wpp : rc_wpr;
-            int c = 0;
-            for (int q = w0 + lane; q < w1; q += 32) c += __popc(cbits[q]);
-            c = warp_sum(c);
+        const int* pcr = rc_pc + (size_t)cslot * P;
+        for (int p = t; p < gp1; p += kT) {
+            const int c = pcr[p];
             if (p >= gp0) {
-                if (lane == 0) {
-                    const long long cA = (long long)p * PW;
-                    const long long cB = cA + PW < B.cols ? cA + PW : B.cols;
-                    s_pc[p - gp0] = c;
-                    s_ph[p - gp0] = hot_rank[cB] - hot_rank[cA];
-                }
+                const long long cA = (long long)p * PW;
+                const long long cB = cA + PW < B.cols ? cA + PW : B.cols;
+                s_pc[p - gp0] = c;
+                s_ph[p - gp0] = hot_rank[cB] - hot_rank[cA];
             } else {
                 before += c;
             }
         }
-        int pass_base = block_sum(lane == 0 ? before : 0, scratch);   // (barrier: s_pc, s_ph ready)
+        int pass_base = block_sum(before, scratch);                   // (barrier: s_pc, s_ph ready)
         int myk = -1, cur = 0;
         float mya = 0.f;
         if (cached && t < na) {
@@ -1855,7 +1851,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     if (w.bhot && w.bpanel) {
         // rows with a cached bitmap: rank-compacted passes, split into
         // p->opts-independent column ranges per row (dense_splits)
-        const bool hotr = w.rc_slot != nullptr && p->hotr_pmax >= 1;
+        const bool hotr = w.rc_slot != nullptr && w.rc_pc != nullptr && p->hotr_pmax >= 1;
         if (hotr) {
             const int pmax_r = p->hotr_pmax < w.panels ? p->hotr_pmax : w.panels;
             const int splits = dense_splits(p, w.panels);
@@ -1864,7 +1860,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                            A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE64_0,
                            NB_DENSE64_0 + NB_DENSE_N, 7, w.bpanel, w.panels, PW, pmax_r,
                            p->hotr_cap, w.hot_rank, w.hot_col, w.bhv, w.rc_slot, w.rc_bits,
-                           w.rc_nslots, w.rc_wpr, splits));
+                           w.rc_pc, w.rc_nslots, w.rc_wpr, splits));
         }
         SPG_LAUNCH(p, K_NUM_DENSE64, s,
                    k_num_dense_hot<<<sms * p->occ_num_dense_hot, kHotThreads, num_dense_hot_smem(p), s>>>(

@@ -275,10 +275,12 @@ __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, Csr
                                                                 int bin_hi, int tier,
                                                                 int nwords, int* rc_slot,
                                                                 unsigned* rc_bits, int rc_nslots,
-                                                                int rc_wpr, int cache_min) {
+                                                                int rc_wpr, int cache_min,
+                                                                int* rc_pc, int P, int wpp) {
     extern __shared__ unsigned bm[];
     __shared__ int s_idx, s_slot;
     __shared__ int red[33];
+    __shared__ int s_pc[kMaxPanels];    // entries per table panel of a one-pass row
     __shared__ ExpandTile<kSymDenseThreads, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
     const long long span_max = (long long)nwords * 32;
@@ -310,9 +312,26 @@ __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, Csr
                     else key_ok(key, B, ctl);
                 });
             int cnt = 0;
-            for (int q = threadIdx.x; q < nw; q += blockDim.x) cnt += __popc(bm[q]);
+            // one-pass rows with a cache: the count by table panel (a warp
+            // per panel), kept for the accumulation phase's pass offsets
+            const bool by_panel = rc_pc != nullptr && c0l == 0 && B.cols <= span_max && P <= kMaxPanels;
+            if (by_panel) {
+                const int lane = lane_id(), nwarp = blockDim.x >> 5;
+                for (int p = threadIdx.x >> 5; p < P; p += nwarp) {
+                    const int w0 = p * wpp, w1 = w0 + wpp < nw ? w0 + wpp : nw;
+                    int c = 0;
+                    for (int q = w0 + lane; q < w1; q += 32) c += __popc(bm[q]);
+                    c = warp_sum(c);
+                    if (lane == 0) {
+                        s_pc[p] = c;
+                        cnt += c;
+                    }
+                }
+            } else {
+                for (int q = threadIdx.x; q < nw; q += blockDim.x) cnt += __popc(bm[q]);
+            }
             nnz += block_sum(cnt, red);
-            // (block_sum ends with a barrier: bm is final here)
+            // (block_sum ends with a barrier: bm and s_pc are final here)
             if (rc_slot != nullptr && c0l == 0 && B.cols <= span_max && nnz > cache_min &&
                 nw == rc_wpr) {
                 if (threadIdx.x == 0) {
@@ -325,6 +344,8 @@ __global__ void __launch_bounds__(kSymDenseThreads, 1) k_sym_dense(CsrDev A, Csr
                 if (slot >= 0) {
                     unsigned* dst = rc_bits + (size_t)slot * rc_wpr;
                     for (int q = threadIdx.x; q < nw; q += blockDim.x) dst[q] = bm[q];
+                    if (by_panel)
+                        for (int p = threadIdx.x; p < P; p += blockDim.x) rc_pc[(size_t)slot * P + p] = s_pc[p];
                 }
             }
         }
@@ -383,7 +404,7 @@ static size_t sym_block_small_smem(const spgemm_plan* p) {
 
 static size_t sym_dense_smem(const spgemm_plan* p) {
     size_t words = kSymDenseWords;
-    const size_t stat = sizeof(ExpandTile<kSymDenseThreads, float>) + 1024;
+    const size_t stat = sizeof(ExpandTile<kSymDenseThreads, float>) + sizeof(int) * kMaxPanels + 1024;
     const size_t cap = (p->smem_optin > stat + 4096 ? p->smem_optin - stat : 4096) / 4;
     if (words > cap) words = cap;
     return words * 4;
@@ -483,7 +504,8 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     SPG_LAUNCH(p, K_SYM_DENSE, s,
                k_sym_dense<<<sms * p->occ_sym_dense, kSymDenseThreads, sd, s>>>(
                    A, B, w.map, w.ctl, row_nnz, SB_DENSE0, SB_DENSE0 + SB_DENSE_N, 1, (int)(sd / 4),
-                   w.rc_slot, w.rc_bits, w.rc_nslots, w.rc_wpr, p->opts.block_max_nnz));
+                   w.rc_slot, w.rc_bits, w.rc_nslots, w.rc_wpr, p->opts.block_max_nnz, w.rc_pc,
+                   w.panels, w.panel_cols / 32));
 }
 
 }  // namespace spg
