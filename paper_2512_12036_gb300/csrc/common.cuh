@@ -312,13 +312,14 @@ __device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long 
     return r;
 }
 
-// Shared-memory staging for block_expand: one tile of kT A entries.
-template <int kT, typename Acc>
+// Shared-memory staging for block_expand: one tile of up to kE A entries
+// (non-empty segments) expanded by kT threads.
+template <int kT, typename Acc, int kE = kT>
 struct ExpandTile {
-    long long off[kT + 1];        // exclusive prefix of segment lengths (non-empty entries)
-    int bs[kT];                   // segment start in B
-    int ln[kT];                   // segment length (padded expansion)
-    Acc a[kT];                    // a_ik (accumulation phase only)
+    long long off[kE + 1];        // exclusive prefix of segment lengths (non-empty entries)
+    int bs[kE];                   // segment start in B
+    int ln[kE];                   // segment length (padded expansion)
+    Acc a[kE];                    // a_ik (accumulation phase only)
     unsigned long long scratch[33];
 };
 
@@ -650,8 +651,10 @@ __device__ __forceinline__ void expand_walk_padded(const Off* off, const int* sb
     }
 }
 
-template <int kT, typename Acc, int kUnroll, bool kSeg = false, class Load, class Apply>
-__device__ __forceinline__ void expand_tile_padded(ExpandTile<kT, Acc>& sm, int bs, int len, Acc a,
+// (A tile of kE < kT entries takes at most kE threads with len > 0; a
+// caller that passes more gets no expansion.)
+template <int kT, typename Acc, int kUnroll, bool kSeg = false, int kE, class Load, class Apply>
+__device__ __forceinline__ void expand_tile_padded(ExpandTile<kT, Acc, kE>& sm, int bs, int len, Acc a,
                                                    Load&& load, Apply&& apply) {
     const int tid = threadIdx.x;
     constexpr int kWarps = kT / 32;
@@ -662,6 +665,10 @@ __device__ __forceinline__ void expand_tile_padded(ExpandTile<kT, Acc>& sm, int 
     const unsigned long long ex = block_excl_scan_u64(v, sm.scratch, &tot);
     const int nE = (int)(tot >> 48);
     const long long P = (long long)(tot & kMask48);    // a multiple of 32
+    if (kE < kT && nE > kE) {                           // block-uniform
+        __syncthreads();
+        return;
+    }
     if (len > 0) {
         const int ci = (int)(ex >> 48);
         sm.off[ci] = (long long)(ex & kMask48);

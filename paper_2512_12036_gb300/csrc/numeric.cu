@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
                                                             int row_begin, int* colC,
                                                             float* valC, int bin_lo, int bin_hi,
                                                             int tier, const int* tab, int P,
-                                                            int PW, int ppp, int only_uncached) {
+                                                            int PW, int ppp, int rank_na) {
     constexpr int kNumDenseThreads = kT;
     const int kPanelsPerPass = kMode == 0 ? ppp : 1;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
         row_extent(A, row, rs, re, ctl);
         const int na = re - rs;
         const bool cached = use_tab && na <= kNumDenseThreads;
-        if (only_uncached && cached) continue;       // the rank-compacted kernel's row
+        if (use_tab && na <= rank_na) continue;      // the rank-compacted kernel's row
         int myk = -1, cur = 0, nxt = 0;
         float mya = 0.f;
         if (cached && (int)threadIdx.x < na) {
@@ -737,6 +737,11 @@ __device__ __forceinline__ void stage_pairs(const unsigned* bm, int* rk, int* st
 // accumulated in word ranges of at most `cap` entries.
 constexpr int kRankPanels = 24;       // 8 and 16 measured slower, 32 leaves too few values
 constexpr int kRankOccUnroll = 8;     // occupancy expansion items are one int
+// A entries a row of this kernel may have (more go to k_num_dense<0>): the
+// fp32 rule keeps dense rows to at most fp32_max_terms (167 by default)
+// entries, and a tile of 256 leaves ~15 KB more for values than one of
+// kD32Threads
+constexpr int kRankTileE = 256;
 // bitmap words a thread holds in registers per pass: kRankPanels panels of
 // at most 16384 columns over kD32Threads threads
 constexpr int kRankWpt = 12;
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
     float* vals = reinterpret_cast<float*>(rk + RW);
     __shared__ int s_idx, s_hi;
     __shared__ int scratch[33];
-    __shared__ ExpandTile<kT, float> tile;
+    __shared__ ExpandTile<kT, float, kRankTileE> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
     if (begin >= end) return;
     if (tab == nullptr || (ctl->b_unsorted & 1) != 0) return;     // fallback kernel's rows
@@ -825,7 +830,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
         int rs, re;
         row_extent(A, row, rs, re, ctl);
         const int na = re - rs;
-        if (na > kT) continue;                        // fallback kernel's row
+        if (na > kRankTileE) continue;                // fallback kernel's row
         int cslot = rc_slot != nullptr ? rc_slot[row] : -1;
         if (cslot >= rc_nslots) {
             set_status(ctl, ST_INTERNAL);
@@ -1841,7 +1846,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
         SPG_LAUNCH(p, K_NUM_DENSE32, s,
                    k_num_dense<0, kD32Threads><<<sms * p->occ_num_dense32, kD32Threads, num_dense_smem(p, 0), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
-                       NB_DENSE32_0 + NB_DENSE_N, 6, w.bpanel, w.panels, PW, p->d32_ppp, 1));
+                       NB_DENSE32_0 + NB_DENSE_N, 6, w.bpanel, w.panels, PW, p->d32_ppp, kRankTileE));
     } else {
         SPG_LAUNCH(p, K_NUM_DENSE32, s,
                    k_num_dense<0, kD32Threads><<<sms * p->occ_num_dense32, kD32Threads, num_dense_smem(p, 0), s>>>(
