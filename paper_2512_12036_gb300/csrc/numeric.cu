@@ -735,17 +735,14 @@ __device__ __forceinline__ void stage_pairs(const unsigned* bm, int* rk, int* st
 // per row so that the expected entries of a pass (nnz_row / P per panel)
 // stay within 3/4 of the value array; a pass that still holds more is
 // accumulated in word ranges of at most `cap` entries.
-constexpr int kRankPanels = 24;       // 8 and 16 measured slower, 32 leaves too few values
+constexpr int kRankPanels = 24;       // 20 and 28 measured slower, 32 leaves too few values
+constexpr int kRankUnroll = 6;        // value expansion: 4 / 5 / 6 / 7 -> 205.6 / 203.3 / 199.6 / 210.9 ms
 constexpr int kRankOccUnroll = 8;     // occupancy expansion items are one int
 // A entries a row of this kernel may have (more go to k_num_dense<0>): the
 // fp32 rule keeps dense rows to at most fp32_max_terms (167 by default)
 // entries, and a tile of 256 leaves ~15 KB more for values than one of
 // kD32Threads
 constexpr int kRankTileE = 256;
-// bitmap words a thread holds in registers per pass: kRankPanels panels of
-// at most 16384 columns over kD32Threads threads
-constexpr int kRankWpt = 12;
-static_assert(kRankPanels * (16384 / 32) <= kRankWpt * kD32Threads, "pass words per thread");
 
 // With a row bitmap cache, a row that holds a slot reads each pass's bitmap
 // words from it (one coalesced copy) instead of the occupancy expansion.
@@ -773,10 +770,6 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
     if (begin >= end) return;
     if (tab == nullptr || (ctl->b_unsorted & 1) != 0) return;     // fallback kernel's rows
     const int t = threadIdx.x;
-    if (RW > kRankWpt * kT) {                         // panels wider than the options allow
-        if (t == 0) set_status(ctl, ST_INTERNAL);
-        return;
-    }
     for (int i = t; i < RW; i += kT) bm[i] = 0u;
     for (int i = t; i < cap; i += kT) vals[i] = 0.f;
     const long long stride = P + 1;
@@ -966,7 +959,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                     if (i < cnt_sub && o < nnz_row) colC[out + o] = stage[i];
                     vals[i] = 0.f;
                 }
-                expand_tile_padded<kT, float, kD32Unroll>(tile, bs, len, mya, load, add);
+                expand_tile_padded<kT, float, kRankUnroll>(tile, bs, len, mya, load, add);
                 for (int i = t; i < cnt_sub; i += kT) {
                     const int o = written + rbase + i;
                     if (o < nnz_row) valC[out + o] = vals[i];
