@@ -204,9 +204,9 @@ class ClockSampler:
 # traffic; a kernel changed since its capture must drop out of this table.
 DRAM_BYTES_PER_PRODUCT = {
     # k_num_dense_hotr (rank-compacted fp64-bound tier with the row bitmap cache)
-    "num_dense64": (987.079168e6 + 346.908928e6) / 256228740,
+    "num_dense64": (974.288640e6 + 344.409856e6) / 256228740,
     # k_num_dense_rank (rank-compacted fp32 tier with the row bitmap cache)
-    "num_dense32": (1100.085e6 + 1083.108e6) / 257686006,
+    "num_dense32": (1099.907e6 + 1066.572e6) / 257686006,
 }
 
 
@@ -686,9 +686,10 @@ def pattern_er4096(device, reps: int = 50):
 
 def row_cache_size(plan, L, A, device) -> int:
     """MiB of row bitmap cache that holds every row of L*A that reaches a
-    dense accumulation tier (one B.cols-bit bitmap per row, plus the slot
-    index of every row), or as much of it as free device memory allows
-    beside the output (8 bytes per entry of C) and 16 GiB of headroom."""
+    dense accumulation tier (one B.cols-bit bitmap and one entry count per
+    column panel per row, plus the slot index of every row), or as much of
+    it as free device memory allows beside the output (8 bytes per entry of
+    C) and 16 GiB of headroom."""
     import torch
     ws = plan.workspace(L, A)
     ip_row, _ = plan.count(L, A, ws)
@@ -696,7 +697,8 @@ def row_cache_size(plan, L, A, device) -> int:
     dense = int((row_nnz > plan.opts["block_max_nnz"]).sum().item())
     del ws, ip_row, row_nnz
     torch.cuda.empty_cache()
-    need = dense * ((A.cols + 31) // 32) * 4 + 4 * L.rows + (1 << 20)
+    panels = -(-A.cols // plan.opts["panel_cols"])
+    need = dense * (((A.cols + 31) // 32) * 4 + 4 * panels) + 4 * L.rows + (1 << 20)
     free, _ = torch.cuda.mem_get_info(device)
     room = free - 8 * nnz - (16 << 30)
     return int(max(0, min(need, room)) >> 20)

@@ -82,7 +82,8 @@ typedef struct {
                                  the dense heavy-row accumulator */
     int32_t row_cache_mb;     /* default 0: MiB of workspace for the allocation phase's
                                  row bitmaps. The allocation phase's bitmap tier keeps the
-                                 column bitmap (B.cols bits) of every row that the
+                                 column bitmap (B.cols bits) and the entry count of each
+                                 column panel (4 bytes per panel) of every row that the
                                  accumulation phase will take in a dense tier, one slot per
                                  row while slots last; the accumulation phase then reads a
                                  row's columns from its slot instead of marking every product

@@ -136,10 +136,15 @@ class Plan:
         if self.opts.get("row_cache_mb", 0) <= 0:
             return 0
         wpr = (B.cols + 31) // 32
-        slot_bytes = (4 * A.rows + 255) // 256 * 256
-        nslots = min(A.rows, max(0, ((self.opts["row_cache_mb"] << 20) - slot_bytes) // (4 * wpr)))
         if wpr == 0 or wpr > 48 * 1024:
-            nslots = 0
+            return 0
+        # the workspace layout: per slot a bitmap and, when B's column panels
+        # have a panel table (at most 1024 panels), one count per panel
+        panels = -(-B.cols // self.opts["panel_cols"])
+        counts = 0 < panels <= 1024
+        slot_bytes = (4 * A.rows + 255) // 256 * 256 + (256 if counts else 0)
+        row_bytes = 4 * wpr + (4 * panels if counts else 0)
+        nslots = min(A.rows, max(0, ((self.opts["row_cache_mb"] << 20) - slot_bytes) // row_bytes))
         used = int(ws[:16].view(torch.int32)[2].item())     # slots asked for (control block)
         return min(used, nslots)
 
