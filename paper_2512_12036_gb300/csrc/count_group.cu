@@ -184,6 +184,7 @@ __device__ __forceinline__ int bin_of(const GroupArgs& g, int r, bool settle) {
     if (g.bcols <= kNarrowCols && ip <= narrow_max_ip(o)) return f64 ? NB_NARROW64 : NB_NARROW32;
     if (nnz <= o.warp_max_nnz && ip <= 16ll * o.warp_max_nnz) return f64 ? NB_WARP64 : NB_WARP32;
     if (nnz <= block_small_nnz(o)) return f64 ? NB_BLOCK64S : NB_BLOCK32S;
+    if (nnz <= block_mid_nnz(o)) return f64 ? NB_BLOCK64M : NB_BLOCK32M;
     if (nnz <= o.block_max_nnz) return f64 ? NB_BLOCK64 : NB_BLOCK32;
     const int L = log2_ceil_ll(ip);
     return (f64 ? NB_DENSE64_0 : NB_DENSE32_0) + clampi(46 - L, 0, NB_DENSE_N - 1);

@@ -38,7 +38,8 @@ struct spgemm_plan {
     // resident blocks per SM for each persistent kernel (filled at creation)
     int occ_sym_warp, occ_sym_block, occ_sym_dense;
     int occ_num_warp32, occ_num_warp64, occ_num_block32, occ_num_block64;
-    int occ_num_block32s, occ_num_block64s;   // small-table launches of the block tier
+    int occ_num_block32s, occ_num_block64s;   // quarter- and half-size table launches of the block tier
+    int occ_num_block32m, occ_num_block64m;
     int occ_num_dense32, occ_num_dense64, occ_num_dense_hot;
     int hot_ppp;           // table panels per pass of the fp64 dense tier
     int d32_ppp;           // and of the fp32 dense tier
@@ -47,6 +48,7 @@ struct spgemm_plan {
     int hotr_cap, hotr_pmax;   // rank-compacted fp64 dense kernel: value slots, panels per pass
     int occ_sym_staged;        // staged block hash tier of the allocation phase
     int occ_sym_block_small;   // its two lighter bins with a quarter-size table
+    int occ_sym_block_mid;     // its second bin with a half-size table
 };
 
 namespace spg {
@@ -71,16 +73,20 @@ constexpr int kMaxPanels = 1024;    // above this the heavy path filters whole B
 //   5..20: dense panels fp32, 21..36: dense panels fp64 (by log2 IP, heavy
 //   first), 39/40: block hash fp32/fp64 for rows of at most a quarter of
 //   block_max_nnz entries (a quarter-size table, several blocks per SM),
+//   41/42: the same for rows of at most half (a half-size table),
 //   63: nothing to do.
 enum : int {
     SB_ESC = 0, SB_WARP = 1, SB_BLOCK0 = 2, SB_BLOCK_N = 4, SB_DENSE0 = 6, SB_DENSE_N = 32,
     NB_ESC = 0, NB_WARP32 = 1, NB_WARP64 = 2, NB_BLOCK32 = 3, NB_BLOCK64 = 4,
     NB_DENSE32_0 = 5, NB_DENSE_N = 16, NB_DENSE64_0 = 21,
-    SB_NARROW = 38, NB_NARROW32 = 37, NB_NARROW64 = 38, NB_BLOCK32S = 39, NB_BLOCK64S = 40
+    SB_NARROW = 38, NB_NARROW32 = 37, NB_NARROW64 = 38, NB_BLOCK32S = 39, NB_BLOCK64S = 40,
+    NB_BLOCK32M = 41, NB_BLOCK64M = 42
 };
 
-// rows of the accumulation block tier that take the small-table launch
+// rows of the accumulation block tier that take the quarter- and half-size
+// table launches
 __host__ __device__ inline int block_small_nnz(const spgemm_opts& o) { return o.block_max_nnz / 4; }
+__host__ __device__ inline int block_mid_nnz(const spgemm_opts& o) { return o.block_max_nnz / 2; }
 
 // Narrow tiers: when B has at most kNarrowCols columns, rows with at most
 // kNarrowMaxIP products take one warp each with a dense per-warp

@@ -1606,6 +1606,10 @@ static size_t num_block_smem_small(const spgemm_plan* p, size_t acc) {
     const unsigned n = (unsigned)block_small_nnz(p->opts);
     return (acc + 4) * pow2_ceil(2u * (n > 32 ? n : 32));
 }
+static size_t num_block_smem_mid(const spgemm_plan* p, size_t acc) {
+    const unsigned n = (unsigned)block_mid_nnz(p->opts);
+    return (acc + 4) * pow2_ceil(2u * (n > 32 ? n : 32));
+}
 static int table_max_bits(size_t slots) {
     int b = 0;
     while (((size_t)1 << b) < slots) ++b;
@@ -1704,6 +1708,8 @@ void occupancy_numeric(spgemm_plan* p) {
         {(const void*)k_num_block<double>, kNumBlockThreads, num_block_smem(p, 8), &p->occ_num_block64},
         {(const void*)k_num_block<float>, kNumBlockThreads, num_block_smem_small(p, 4), &p->occ_num_block32s},
         {(const void*)k_num_block<double>, kNumBlockThreads, num_block_smem_small(p, 8), &p->occ_num_block64s},
+        {(const void*)k_num_block<float>, kNumBlockThreads, num_block_smem_mid(p, 4), &p->occ_num_block32m},
+        {(const void*)k_num_block<double>, kNumBlockThreads, num_block_smem_mid(p, 8), &p->occ_num_block64m},
         {(const void*)k_num_dense<0, kD32Threads>, kD32Threads, num_dense_smem(p, 0), &p->occ_num_dense32},
         {(const void*)k_num_dense<1, 1024>, 1024, num_dense_smem(p, 1), &p->occ_num_dense64},
         {(const void*)k_num_dense_hot, kHotThreads, num_dense_hot_smem(p), &p->occ_num_dense_hot},
@@ -1802,14 +1808,19 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     SPG_LAUNCH(p, K_NUM_WARP64, s,
                k_num_warp<double><<<sms * p->occ_num_warp64, kWarpsPerBlockNW * 32, num_warp_smem(8), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_WARP64, hash_load(p)));
-    // block hash tier: rows of more than a quarter of block_max_nnz entries
-    // with the full table (one block per SM), the others with a quarter-size
-    // table and as many blocks per SM as it leaves room for
+    // block hash tier: rows of more than half of block_max_nnz entries with
+    // the full table (one block per SM), the others with a half- or
+    // quarter-size table and as many blocks per SM as it leaves room for
     const int max_bits = table_max_bits(num_block_smem(p, 4) / 8);
+    const int mid_bits = table_max_bits(num_block_smem_mid(p, 4) / 8);
     const int small_bits = table_max_bits(num_block_smem_small(p, 4) / 8);
     SPG_LAUNCH(p, K_NUM_BLOCK32, s,
                k_num_block<float><<<sms * p->occ_num_block32, kNumBlockThreads, num_block_smem(p, 4), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK32, 2, max_bits,
+                   hash_load(p)));
+    SPG_LAUNCH(p, K_NUM_BLOCK32, s,
+               k_num_block<float><<<sms * p->occ_num_block32m, kNumBlockThreads, num_block_smem_mid(p, 4), s>>>(
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK32M, 10, mid_bits,
                    hash_load(p)));
     SPG_LAUNCH(p, K_NUM_BLOCK32, s,
                k_num_block<float><<<sms * p->occ_num_block32s, kNumBlockThreads, num_block_smem_small(p, 4), s>>>(
@@ -1818,6 +1829,10 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     SPG_LAUNCH(p, K_NUM_BLOCK64, s,
                k_num_block<double><<<sms * p->occ_num_block64, kNumBlockThreads, num_block_smem(p, 8), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits,
+                   hash_load(p)));
+    SPG_LAUNCH(p, K_NUM_BLOCK64, s,
+               k_num_block<double><<<sms * p->occ_num_block64m, kNumBlockThreads, num_block_smem_mid(p, 8), s>>>(
+                   A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64M, 11, mid_bits,
                    hash_load(p)));
     SPG_LAUNCH(p, K_NUM_BLOCK64, s,
                k_num_block<double><<<sms * p->occ_num_block64s, kNumBlockThreads, num_block_smem_small(p, 8), s>>>(

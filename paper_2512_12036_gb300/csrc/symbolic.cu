@@ -401,6 +401,12 @@ static size_t sym_block_small_smem(const spgemm_plan* p) {
     const int bits = Lmax - 1 > 6 ? Lmax - 1 : 6;
     return (size_t)4 << bits;
 }
+// and of its second bin (at most 2^(Lmax - 1) products)
+static size_t sym_block_mid_smem(const spgemm_plan* p) {
+    const int Lmax = log2_ceil_ll(p->opts.block_max_ip);
+    const int bits = Lmax > 6 ? Lmax : 6;
+    return (size_t)4 << bits;
+}
 
 static size_t sym_dense_smem(const spgemm_plan* p) {
     size_t words = kSymDenseWords;
@@ -430,6 +436,9 @@ void occupancy_symbolic(spgemm_plan* p) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block_small, k_sym_block,
                                                   kSymBlockThreads, sym_block_small_smem(p));
     if (p->occ_sym_block_small < 1) p->occ_sym_block_small = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block_mid, k_sym_block,
+                                                  kSymBlockThreads, sym_block_mid_smem(p));
+    if (p->occ_sym_block_mid < 1) p->occ_sym_block_mid = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_dense, k_sym_dense,
                                                   kSymDenseThreads, sd);
     if (p->occ_sym_warp < 1) p->occ_sym_warp = 1;
@@ -473,14 +482,25 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
                 break;
             }
     }
-    // bins SB_BLOCK0 and +1 with the full table (one block per SM), the two
-    // lighter bins (IP at most a quarter of block_max_ip) with a quarter-size
-    // table and several blocks per SM
+    // bin SB_BLOCK0 with the full table (one block per SM), bin +1 (IP at
+    // most half of block_max_ip) with a half-size table, the two lighter
+    // bins (at most a quarter) with a quarter-size table: the smaller the
+    // table, the more blocks share an SM
+    const int mid = staged_lo < SB_BLOCK0 + 1 ? staged_lo : SB_BLOCK0 + 1;
     const int split = staged_lo < SB_BLOCK0 + 2 ? staged_lo : SB_BLOCK0 + 2;
     SPG_LAUNCH(p, K_SYM_BLOCK, s,
                k_sym_block<<<sms * p->occ_sym_block, kSymBlockThreads, (size_t)tb * 4, s>>>(
-                   A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, split, 0, max_bits,
+                   A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, mid, 0, max_bits,
                    hash_load(p)));
+    if (mid < split) {
+        const size_t sm = sym_block_mid_smem(p);
+        int mid_bits = 0;
+        while (((size_t)4 << mid_bits) < sm) ++mid_bits;
+        SPG_LAUNCH(p, K_SYM_BLOCK, s,
+                   k_sym_block<<<sms * p->occ_sym_block_mid, kSymBlockThreads, sm, s>>>(
+                       A, B, ip, w.map, w.ctl, row_nnz, mid, split, 4, mid_bits,
+                       hash_load(p)));
+    }
     if (split < staged_lo) {
         const size_t ss = sym_block_small_smem(p);
         int small_bits = 0;

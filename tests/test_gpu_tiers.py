@@ -1,9 +1,9 @@
 """Row routing between kernels of one tier, against the oracle:
 
 - the block hash tiers run rows of at most a quarter of their limit with a
-  quarter-size table (allocation: IP at most block_max_ip / 4;
-  accumulation: nnz at most block_max_nnz / 4, fp32 and fp64 alike) and the
-  rest with the full table;
+  quarter-size table, rows of at most half with a half-size table and the
+  rest with the full table (allocation: by IP against block_max_ip;
+  accumulation: by nnz against block_max_nnz, fp32 and fp64 alike);
 - the fp32 dense tier's rank-compacted kernel takes rows of at most 256 A
   entries (its expansion tile), the fallback dense-array kernel the others,
   with and without the row bitmap cache (rows of more than 256 entries reach
@@ -48,7 +48,7 @@ def rows_from_groups(spec, groups, k_rows, seed):
     return gen.csr_from_coo(len(spec), k_rows, r, c, gen.uniform_open_closed(rng, r.size))
 
 
-def test_block_tiers_both_table_sizes():
+def test_block_tiers_all_table_sizes():
     # B groups: rows of 8, 30, 50 and 120 entries over 200,000 columns, and
     # rows of 40 entries over 3,000 columns (products that meet)
     B1, g1 = grouped_b(200_000, [8, 30, 50, 120], 400, seed=5)
@@ -68,7 +68,8 @@ def test_block_tiers_both_table_sizes():
                  (200, 0),      # fp64 (> 167 entries), IP 1600: small table
                  (300, 1),      # fp64, IP 9000: full tables
                  (150, 4),      # fp32, IP 6000 into 3000 columns (many products meet)
-                 (250, 4)]      # fp64, IP 10000 into 3000 columns
+                 (250, 4),      # fp64, IP 10000 into 3000 columns
+                 (240, 1)]      # fp64, IP 7200
     A = rows_from_groups(spec, groups, B.rows, seed=7)
     plan = Plan()
     ip, _ = oracle.ip_count(A, B)
@@ -77,13 +78,16 @@ def test_block_tiers_both_table_sizes():
     na = np.diff(A.row_ptr)
     block = (nnz > o["warp_max_nnz"]) & (nnz <= o["block_max_nnz"])
     small = block & (nnz <= o["block_max_nnz"] // 4)
+    mid = block & ~small & (nnz <= o["block_max_nnz"] // 2)
+    large = block & ~small & ~mid
     f64 = (na > o["fp32_max_terms"]) & (ip > o["fp32_max_terms"])
-    # every accumulation class is present, and both allocation table sizes
-    for m in (small & ~f64, small & f64, block & ~small & ~f64, block & ~small & f64):
-        assert m.sum() >= 6
+    # every accumulation class is present, and every allocation table size
+    for m in (small, mid, large):
+        assert (m & ~f64).sum() >= 6 and (m & f64).sum() >= 6
     sym_block = (ip > o["warp_max_ip"]) & (ip <= o["block_max_ip"])
     assert (sym_block & (ip <= o["block_max_ip"] // 4)).sum() >= 6
-    assert (sym_block & (ip > o["block_max_ip"] // 4)).sum() >= 6
+    assert (sym_block & (ip > o["block_max_ip"] // 4) & (ip <= o["block_max_ip"] // 2)).sum() >= 6
+    assert (sym_block & (ip > o["block_max_ip"] // 2)).sum() >= 6
     dA, dB = DeviceCSR.from_host(A), DeviceCSR.from_host(B)
     C = plan.spgemm(dA, dB)
     torch.cuda.synchronize()
