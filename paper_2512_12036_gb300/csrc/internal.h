@@ -62,6 +62,7 @@ constexpr int kWarpsPerBlockNW = 8;
 constexpr int kSymBlockThreads = 512;
 constexpr int kSymDenseThreads = 1024;
 constexpr int kNumBlockThreads = 512;
+constexpr int kBlockThreadsFull = 1024;   // block tiers' full-size-table launches
 constexpr int kNumDenseThreads = 1024;
 constexpr int kMaxPanels = 1024;    // above this the heavy path filters whole B rows
 

@@ -355,8 +355,11 @@ __global__ void __launch_bounds__(kNarrowMaxWarps * 32) k_num_narrow(CsrDev A, C
 }
 
 // ---------------------------------------------------------------------------
-template <typename Acc>
-__global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev B,
+// kT threads per block: kNumBlockThreads, or kBlockThreadsFull for the
+// launch whose full-size table leaves one block per SM (more warps to hide
+// latency with)
+template <typename Acc, int kT = kNumBlockThreads>
+__global__ void __launch_bounds__(kT) k_num_block(CsrDev A, CsrDev B,
                                                                 const int* map, Ctl* ctl,
                                                                 const int* rptC, int row_begin,
                                                                 int* colC, float* valC, int bin,
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev
     __shared__ int scratch[33];
     __shared__ int s_cnt[kSortBuckets];
     __shared__ int s_mm[3];
-    __shared__ ExpandTile<kNumBlockThreads, Acc> tile;
+    __shared__ ExpandTile<kT, Acc> tile;
     const int begin = ctl->bin_off[bin], end = ctl->bin_off[bin + 1];
     for (;;) {
         if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(kNumBlockThreads) k_num_block(CsrDev A, CsrDev
         __syncthreads();
         int rs, re;
         row_extent(A, row, rs, re, ctl);
-        block_expand<kNumBlockThreads, Acc, 2>(
+        block_expand<kT, Acc, 2>(
             rs, re, tile,
             [&](int j, int& bs, int& len, Acc& a) {
                 a_entry(A, B, j, bs, len, ctl);
@@ -1704,8 +1707,10 @@ void occupancy_numeric(spgemm_plan* p) {
          &p->occ_num_rank},
         {(const void*)k_num_warp<float>, kWarpsPerBlockNW * 32, num_warp_smem(4), &p->occ_num_warp32},
         {(const void*)k_num_warp<double>, kWarpsPerBlockNW * 32, num_warp_smem(8), &p->occ_num_warp64},
-        {(const void*)k_num_block<float>, kNumBlockThreads, num_block_smem(p, 4), &p->occ_num_block32},
-        {(const void*)k_num_block<double>, kNumBlockThreads, num_block_smem(p, 8), &p->occ_num_block64},
+        {(const void*)k_num_block<float, kBlockThreadsFull>, kBlockThreadsFull, num_block_smem(p, 4),
+         &p->occ_num_block32},
+        {(const void*)k_num_block<double, kBlockThreadsFull>, kBlockThreadsFull, num_block_smem(p, 8),
+         &p->occ_num_block64},
         {(const void*)k_num_block<float>, kNumBlockThreads, num_block_smem_small(p, 4), &p->occ_num_block32s},
         {(const void*)k_num_block<double>, kNumBlockThreads, num_block_smem_small(p, 8), &p->occ_num_block64s},
         {(const void*)k_num_block<float>, kNumBlockThreads, num_block_smem_mid(p, 4), &p->occ_num_block32m},
@@ -1815,7 +1820,8 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     const int mid_bits = table_max_bits(num_block_smem_mid(p, 4) / 8);
     const int small_bits = table_max_bits(num_block_smem_small(p, 4) / 8);
     SPG_LAUNCH(p, K_NUM_BLOCK32, s,
-               k_num_block<float><<<sms * p->occ_num_block32, kNumBlockThreads, num_block_smem(p, 4), s>>>(
+               k_num_block<float, kBlockThreadsFull><<<sms * p->occ_num_block32, kBlockThreadsFull,
+                                                      num_block_smem(p, 4), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK32, 2, max_bits,
                    hash_load(p)));
     SPG_LAUNCH(p, K_NUM_BLOCK32, s,
@@ -1827,7 +1833,8 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK32S, 8, small_bits,
                    hash_load(p)));
     SPG_LAUNCH(p, K_NUM_BLOCK64, s,
-               k_num_block<double><<<sms * p->occ_num_block64, kNumBlockThreads, num_block_smem(p, 8), s>>>(
+               k_num_block<double, kBlockThreadsFull><<<sms * p->occ_num_block64, kBlockThreadsFull,
+                                                       num_block_smem(p, 8), s>>>(
                    A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_BLOCK64, 3, max_bits,
                    hash_load(p)));
     SPG_LAUNCH(p, K_NUM_BLOCK64, s,

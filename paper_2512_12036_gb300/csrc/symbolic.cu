@@ -110,7 +110,10 @@ __global__ void __launch_bounds__(kWarpsPerBlockSW * 32) k_sym_warp(CsrDev A, Cs
 }
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev B,
+// kT threads per block: kSymBlockThreads, or kBlockThreadsFull for the
+// full-size table's launch (one block per SM)
+template <int kT>
+__global__ void __launch_bounds__(kT) k_sym_block(CsrDev A, CsrDev B,
                                                                 const long long* ip,
                                                                 const int* map, Ctl* ctl,
                                                                 int* row_nnz, int bin_lo,
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev
     extern __shared__ int table[];
     __shared__ int s_idx;
     __shared__ int red[33];
-    __shared__ ExpandTile<kSymBlockThreads, float> tile;
+    __shared__ ExpandTile<kT, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
     for (;;) {
         if (threadIdx.x == 0) s_idx = begin + atomicAdd(&ctl->work[tier], 1);
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(kSymBlockThreads) k_sym_block(CsrDev A, CsrDev
         int rs, re;
         row_extent(A, row, rs, re, ctl);
         int cnt = 0;
-        block_expand<kSymBlockThreads, float, 2>(
+        block_expand<kT, float, 2>(
             rs, re, tile,
             [&](int j, int& bs, int& len, float&) { a_entry(A, B, j, bs, len, ctl); },
             [&](int t) { return B.col[t]; },
@@ -427,16 +430,17 @@ void occupancy_symbolic(spgemm_plan* p) {
     const size_t sb = (size_t)pow2_ceil(2u * (unsigned)p->opts.block_max_ip) * 4;
     const size_t sd = sym_dense_smem(p);
     allow_max_dynamic_smem((const void*)k_sym_warp, p);
-    allow_max_dynamic_smem((const void*)k_sym_block, p);
+    allow_max_dynamic_smem((const void*)k_sym_block<kBlockThreadsFull>, p);
+    allow_max_dynamic_smem((const void*)k_sym_block<kSymBlockThreads>, p);
     allow_max_dynamic_smem((const void*)k_sym_dense, p);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_warp, k_sym_warp,
                                                   kWarpsPerBlockSW * 32, sw);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block, k_sym_block,
-                                                  kSymBlockThreads, sb);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block_small, k_sym_block,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block, k_sym_block<kBlockThreadsFull>,
+                                                  kBlockThreadsFull, sb);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block_small, k_sym_block<kSymBlockThreads>,
                                                   kSymBlockThreads, sym_block_small_smem(p));
     if (p->occ_sym_block_small < 1) p->occ_sym_block_small = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block_mid, k_sym_block,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_block_mid, k_sym_block<kSymBlockThreads>,
                                                   kSymBlockThreads, sym_block_mid_smem(p));
     if (p->occ_sym_block_mid < 1) p->occ_sym_block_mid = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occ_sym_dense, k_sym_dense,
@@ -489,7 +493,7 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
     const int mid = staged_lo < SB_BLOCK0 + 1 ? staged_lo : SB_BLOCK0 + 1;
     const int split = staged_lo < SB_BLOCK0 + 2 ? staged_lo : SB_BLOCK0 + 2;
     SPG_LAUNCH(p, K_SYM_BLOCK, s,
-               k_sym_block<<<sms * p->occ_sym_block, kSymBlockThreads, (size_t)tb * 4, s>>>(
+               k_sym_block<kBlockThreadsFull><<<sms * p->occ_sym_block, kBlockThreadsFull, (size_t)tb * 4, s>>>(
                    A, B, ip, w.map, w.ctl, row_nnz, SB_BLOCK0, mid, 0, max_bits,
                    hash_load(p)));
     if (mid < split) {
@@ -497,7 +501,7 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
         int mid_bits = 0;
         while (((size_t)4 << mid_bits) < sm) ++mid_bits;
         SPG_LAUNCH(p, K_SYM_BLOCK, s,
-                   k_sym_block<<<sms * p->occ_sym_block_mid, kSymBlockThreads, sm, s>>>(
+                   k_sym_block<kSymBlockThreads><<<sms * p->occ_sym_block_mid, kSymBlockThreads, sm, s>>>(
                        A, B, ip, w.map, w.ctl, row_nnz, mid, split, 4, mid_bits,
                        hash_load(p)));
     }
@@ -506,7 +510,7 @@ void launch_symbolic(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, con
         int small_bits = 0;
         while (((size_t)4 << small_bits) < ss) ++small_bits;
         SPG_LAUNCH(p, K_SYM_BLOCK, s,
-                   k_sym_block<<<sms * p->occ_sym_block_small, kSymBlockThreads, ss, s>>>(
+                   k_sym_block<kSymBlockThreads><<<sms * p->occ_sym_block_small, kSymBlockThreads, ss, s>>>(
                        A, B, ip, w.map, w.ctl, row_nnz, split, staged_lo, 3, small_bits,
                        hash_load(p)));
     }
