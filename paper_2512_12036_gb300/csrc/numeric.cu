@@ -1531,18 +1531,21 @@ __global__ void __launch_bounds__(kHotrThreads, 1) k_num_dense_hotr(
                         int tbs = 0, tlen = 0;
                         float a = 0.f;
                         if (j < re) {
-                            a_entry(A, B, j, tbs, tlen, ctl);
+                            // the pass's segment straight from the panel table
+                            // (two dependent loads: the entry, then its offsets)
+                            const int k = A.col[j];
                             a = A.val[j];
-                            if (tlen > 0) {
-                                const int* tk = tab + (long long)A.col[j] * stride;
+                            if ((unsigned)k < (unsigned)B.rows) {
+                                const int* tk = tab + (long long)k * stride;
                                 const int ps = tk[p0], pe = tk[p1];
-                                if (ps >= tbs && pe >= ps && pe <= tbs + tlen) {
+                                if (ps >= 0 && pe >= ps && (long long)pe <= B.nnz) {
                                     tbs = ps;
                                     tlen = pe - ps;
                                 } else {
                                     set_status(ctl, ST_INTERNAL);
-                                    tlen = 0;
                                 }
+                            } else {
+                                set_status(ctl, ST_INVALID);
                             }
                         }
                         expand_tile<kT, float, kHotrUnroll, true>(tile, tbs, tlen, a, load, apply);
