@@ -14,7 +14,8 @@
 
 namespace spg {
 
-constexpr int kSymDenseUnroll = 6;   // products per warp step batch (4 and 8 measured slower)
+constexpr int kSymDenseUnroll = 6;   // products per warp step batch (4 / 6 / 8 -> 108.5 / 101.7 / 103.4 ms)
+constexpr int kSymBlockUnroll = 4;   // block hash tier (2 / 4 -> 11.8 / 11.2 ms)
 
 constexpr int kSymDenseWords = 48 * 1024;   // 192 KB bitmap (1.5M columns per pass)
 
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kT) k_sym_block(CsrDev A, CsrDev B,
         int rs, re;
         row_extent(A, row, rs, re, ctl);
         int cnt = 0;
-        block_expand<kT, float, 2>(
+        block_expand<kT, float, kSymBlockUnroll>(
             rs, re, tile,
             [&](int j, int& bs, int& len, float&) { a_entry(A, B, j, bs, len, ctl); },
             [&](int t) { return B.col[t]; },
