@@ -29,7 +29,8 @@ struct Ctl {
     int b_unsorted;             // bit 0: a row of B is not sorted by column;
                                 // bit 1: a sorted row of B repeats a column
     int rc_used;                // row bitmap cache slots handed out
-    int pad0;
+    int dense_wide;             // accumulation grouping: a row of the fp32 dense tier has
+                                // more A entries than the rank-compacted kernel takes
     long long totals[8];        // 0: IP total, 1: nnz total, 2: scan total
     int work[kMaxTiers];        // dynamic row counters of the block-per-row tiers
     int bin_off[kNumBins + 1];  // start of every bin in the row map

@@ -225,10 +225,12 @@ __global__ void __launch_bounds__(1024) k_group_scan(int nblk, int* blk_counts, 
         if (offsets_out && b <= ngroups) offsets_out[b] = b == ngroups ? carry : off;
     }
     if (threadIdx.x < kMaxTiers) ctl->work[threadIdx.x] = 0;
+    if (threadIdx.x == 0) ctl->dense_wide = 0;
 }
 
 __global__ void __launch_bounds__(kBinRows) k_group_scatter(GroupArgs g, int nblk,
-                                                            const int* blk_counts, int* map) {
+                                                            const int* blk_counts, int* map,
+                                                            Ctl* ctl) {
     __shared__ int wcount[kBinRows / 32][kNumBins];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     for (int i = threadIdx.x; i < (kBinRows / 32) * kNumBins; i += blockDim.x)
@@ -236,6 +238,12 @@ __global__ void __launch_bounds__(kBinRows) k_group_scatter(GroupArgs g, int nbl
     __syncthreads();
     const int r = blockIdx.x * kBinRows + threadIdx.x;
     const int b = r < g.n ? bin_of(g, r, false) : -1;
+    // accumulation: flag an fp32 dense row too wide for the rank-compacted
+    // kernel, so the fallback kernel runs only when it has rows
+    if (g.phase == 1 && b >= NB_DENSE32_0 && b < NB_DENSE32_0 + NB_DENSE_N) {
+        const int row = g.row_begin + r;
+        if (g.rptA[row + 1] - g.rptA[row] > kRankTileEntries) ctl->dense_wide = 1;
+    }
     const unsigned peers = __match_any_sync(kFull, b);
     const int rank = __popc(peers & lanemask_lt());
     if (b >= 0 && rank == 0) wcount[warp][b] = __popc(peers);
@@ -262,7 +270,7 @@ void launch_group(const spgemm_plan* p, const GroupArgs& g, const WsPtrs& w, int
                                                g.phase == 2 ? g.nthr + 1 : 0));
     if (nblk > 0)
         SPG_LAUNCH(p, K_GROUP_SCATTER, s,
-                   k_group_scatter<<<nblk, kBinRows, 0, s>>>(g, nblk, w.blk_counts, map_out));
+                   k_group_scatter<<<nblk, kBinRows, 0, s>>>(g, nblk, w.blk_counts, map_out, w.ctl));
 }
 
 // ---------------------------------------------------------------------------

@@ -63,6 +63,9 @@ constexpr int kSymBlockThreads = 512;
 constexpr int kSymDenseThreads = 1024;
 constexpr int kNumBlockThreads = 512;
 constexpr int kBlockThreadsFull = 1024;   // block tiers' full-size-table launches
+// A entries a row of the fp32 rank-compacted dense kernel may have (its
+// expansion tile); rows with more take the dense-array fallback kernel
+constexpr int kRankTileEntries = 256;
 constexpr int kNumDenseThreads = 1024;
 constexpr int kMaxPanels = 1024;    // above this the heavy path filters whole B rows
 

@@ -534,6 +534,10 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
     __shared__ ExpandTile<kNumDenseThreads, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
     if (begin >= end) return;
+    const bool use_tab = tab != nullptr && (ctl->b_unsorted & 1) == 0;
+    // beside the rank-compacted kernel, only rows wider than its tile are
+    // this kernel's; the grouping flags whether there are any
+    if (rank_na > 0 && use_tab && ctl->dense_wide == 0) return;
     const int wpt = (nwords_pass + kNumDenseThreads - 1) / kNumDenseThreads;   // words per thread
     const int w0 = threadIdx.x * wpt;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -544,7 +548,6 @@ __global__ void __launch_bounds__(kT, 1024 / kT) k_num_dense(CsrDev A, CsrDev B,
         bm[i] = 0u;
         if (kMode == 1) gbm[i] = 0u;
     }
-    const bool use_tab = tab != nullptr && (ctl->b_unsorted & 1) == 0;
     const int npass = (int)((B.cols + (long long)W - 1) / W);
     const long long stride = P + 1;
     unsigned* obm = kMode == 1 ? gbm : bm;             // bitmap the products mark
@@ -746,7 +749,7 @@ constexpr int kRankOccUnroll = 8;     // occupancy expansion items are one int
 // fp32 rule keeps dense rows to at most fp32_max_terms (167 by default)
 // entries, and a tile of 256 leaves ~15 KB more for values than one of
 // kD32Threads
-constexpr int kRankTileE = 256;
+constexpr int kRankTileE = kRankTileEntries;
 
 // With a row bitmap cache, a row that holds a slot reads each pass's bitmap
 // words from it (one coalesced copy) instead of the occupancy expansion.
