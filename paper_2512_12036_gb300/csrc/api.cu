@@ -1,4 +1,5 @@
 // C ABI of libspgemm: argument checks, workspace layout and phase order.
+#include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -208,12 +209,9 @@ static int map_status(int bits) {
 
 // Synchronise, fetch totals[which] (if out) and the status word, clear it.
 static int sync_read(Ctl* ctl, int which, int64_t* out, cudaStream_t s) {
-    struct {
-        int status;
-        int pad[3];
-        long long totals[8];
-    } h;
-    cudaError_t e = cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s);
+    Ctl h;                                   // its head, up to and including the totals
+    cudaError_t e = cudaMemcpyAsync(&h, ctl, offsetof(Ctl, totals) + sizeof(h.totals),
+                                    cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return SPGEMM_ERR_CUDA;
     if (out && which >= 0) *out = h.totals[which];

@@ -31,10 +31,13 @@ struct Ctl {
     int rc_used;                // row bitmap cache slots handed out
     int dense_wide;             // accumulation grouping: a row of the fp32 dense tier has
                                 // more A entries than the rank-compacted kernel takes
+    int dense_uncached;         // accumulation grouping: a row of the fp64-bound dense tier
+                                // has no cached bitmap
+    int pad0;
     long long totals[8];        // 0: IP total, 1: nnz total, 2: scan total
     int work[kMaxTiers];        // dynamic row counters of the block-per-row tiers
     int bin_off[kNumBins + 1];  // start of every bin in the row map
-    int pad1[256 - 4 - 16 - kMaxTiers - (kNumBins + 1)];
+    int pad1[256 - 6 - 16 - kMaxTiers - (kNumBins + 1)];
 };
 static_assert(sizeof(Ctl) % 256 == 0, "Ctl must keep the following arrays aligned");
 

@@ -225,7 +225,10 @@ __global__ void __launch_bounds__(1024) k_group_scan(int nblk, int* blk_counts, 
         if (offsets_out && b <= ngroups) offsets_out[b] = b == ngroups ? carry : off;
     }
     if (threadIdx.x < kMaxTiers) ctl->work[threadIdx.x] = 0;
-    if (threadIdx.x == 0) ctl->dense_wide = 0;
+    if (threadIdx.x == 0) {
+        ctl->dense_wide = 0;
+        ctl->dense_uncached = 0;
+    }
 }
 
 __global__ void __launch_bounds__(kBinRows) k_group_scatter(GroupArgs g, int nblk,
@@ -240,10 +243,15 @@ __global__ void __launch_bounds__(kBinRows) k_group_scatter(GroupArgs g, int nbl
     const int b = r < g.n ? bin_of(g, r, false) : -1;
     // accumulation: flag an fp32 dense row too wide for the rank-compacted
     // kernel, so the fallback kernel runs only when it has rows
+    // and an fp64-bound dense row without a cached bitmap, so the kernel
+    // for those runs only when there are some
     if (g.phase == 1 && b >= NB_DENSE32_0 && b < NB_DENSE32_0 + NB_DENSE_N) {
         const int row = g.row_begin + r;
         if (g.rptA[row + 1] - g.rptA[row] > kRankTileEntries) ctl->dense_wide = 1;
     }
+    if (g.phase == 1 && b >= NB_DENSE64_0 && b < NB_DENSE64_0 + NB_DENSE_N &&
+        (g.rc_slot == nullptr || g.rc_slot[g.row_begin + r] < 0))
+        ctl->dense_uncached = 1;
     const unsigned peers = __match_any_sync(kFull, b);
     const int rank = __popc(peers & lanemask_lt());
     if (b >= 0 && rank == 0) wcount[warp][b] = __popc(peers);

@@ -183,6 +183,7 @@ struct GroupArgs {
     const long long* thr;      // generic: thresholds
     int nthr;
     int bcols;                 // columns of B (narrow tiers, backward dense tier)
+    const int* rc_slot;        // accumulation: row bitmap cache slots, or nullptr
     spgemm_opts opts;
 };
 void launch_group(const spgemm_plan* p, const GroupArgs& g, const WsPtrs& w, int* map_out,

@@ -1036,6 +1036,9 @@ __global__ void __launch_bounds__(kHotThreads, 1) k_num_dense_hot(CsrDev A, CsrD
     __shared__ ExpandTile<kHotThreads, float> tile;
     const int begin = ctl->bin_off[bin_lo], end = ctl->bin_off[bin_hi];
     if (begin >= end) return;
+    // beside k_num_dense_hotr, only rows without a cached bitmap are this
+    // kernel's; the grouping flags whether there are any
+    if (skip_cached && ctl->dense_uncached == 0) return;
     const int t = threadIdx.x;
     const int nwords = W >> 5;
     for (int i = t; i < kHotSlots / 32; i += kHotThreads) touched[i] = 0u;
@@ -1796,6 +1799,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     g.rptA = A.rpt;
     g.rptC = rptC;
     g.bcols = B.cols;
+    g.rc_slot = w.rc_slot;
     g.opts = p->opts;
     launch_group(p, g, w, w.map, nullptr, s);
     if (g.n == 0) return;
