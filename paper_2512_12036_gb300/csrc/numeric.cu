@@ -744,6 +744,11 @@ __device__ __forceinline__ void stage_pairs(const unsigned* bm, int* rk, int* st
 // 196.1 / 195.0 ms; on another box 95 / 100 / 110% 193.4 / 193.8 / 226.6
 // ms); a pass that still holds more is accumulated in word ranges of at
 // most `cap` entries.
+// two 512-thread blocks per SM, each with half of the SM's shared memory
+// (12 panels per pass, ~15K values), instead of one of 1024: one block's
+// barriers and scans overlap the other's walk (193.4 -> 181.1 ms)
+constexpr int kRankThreads = 512;
+constexpr int kRankBlocks = 2;                    // per SM
 constexpr int kRankPanels = 24;       // 20 and 28 measured slower, 32 leaves too few values
 constexpr int kRankUnroll = 6;        // value expansion: 4 / 5 / 6 / 7 -> 205.6 / 203.3 / 199.6 / 210.9 ms
 constexpr int kRankOccUnroll = 8;     // occupancy expansion items are one int
@@ -755,7 +760,7 @@ constexpr int kRankTileE = kRankTileEntries;
 
 // With a row bitmap cache, a row that holds a slot reads each pass's bitmap
 // words from it (one coalesced copy) instead of the occupancy expansion.
-__global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, CsrDev B,
+__global__ void __launch_bounds__(kRankThreads, kRankBlocks) k_num_dense_rank(CsrDev A, CsrDev B,
                                                                    const int* map, Ctl* ctl,
                                                                    const int* rptC, int row_begin,
                                                                    int* colC, float* valC,
@@ -766,7 +771,7 @@ __global__ void __launch_bounds__(kD32Threads, 1) k_num_dense_rank(CsrDev A, Csr
                                                                    const unsigned* rc_bits,
                                                                    int rc_nslots, int rc_wpr,
                                                                    const int2* bcv) {
-    constexpr int kT = kD32Threads;
+    constexpr int kT = kRankThreads;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int RW = (pmax * PW) >> 5;                  // words of the widest pass
     unsigned* bm = reinterpret_cast<unsigned*>(sm_raw);
@@ -1693,7 +1698,13 @@ void occupancy_numeric(spgemm_plan* p) {
     {
         cudaFuncAttributes fa{};
         cudaFuncGetAttributes(&fa, (const void*)k_num_dense_rank);
-        p->rank_budget = p->smem_optin > fa.sharedSizeBytes ? p->smem_optin - fa.sharedSizeBytes : 0;
+        int per_sm = 0, reserved = 0;
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, p->device);
+        size_t avail = (size_t)per_sm / kRankBlocks;
+        avail = avail > (size_t)reserved ? avail - reserved : 0;
+        if (avail > p->smem_optin) avail = p->smem_optin;
+        p->rank_budget = avail > fa.sharedSizeBytes ? avail - fa.sharedSizeBytes : 0;
     }
     // rank-compacted fp64 tier: 20480 value slots (at least one panel), as
     // many panels per pass as the rest of shared memory holds
@@ -1715,8 +1726,8 @@ void occupancy_numeric(spgemm_plan* p) {
         size_t smem;
         int* occ;
     } ks[] = {
-        {(const void*)k_num_dense_rank, kD32Threads, rank_smem(p, kRankPanels, p->opts.panel_cols),
-         &p->occ_num_rank},
+        {(const void*)k_num_dense_rank, kRankThreads,
+         rank_smem(p, kRankPanels / kRankBlocks, p->opts.panel_cols), &p->occ_num_rank},
         {(const void*)k_num_warp<float>, kWarpsPerBlockNW * 32, num_warp_smem(4), &p->occ_num_warp32},
         {(const void*)k_num_warp<double>, kWarpsPerBlockNW * 32, num_warp_smem(8), &p->occ_num_warp64},
         {(const void*)k_num_block<float, kBlockThreadsFull>, kBlockThreadsFull, num_block_smem(p, 4),
@@ -1861,13 +1872,13 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     const int PW = w.panel_cols;
     if (w.bhv && w.bpanel && B.nnz > 0)
         SPG_LAUNCH(p, K_HOT, s, k_pack_b<<<sms * 8, 256, 0, s>>>(B, w.bhot, w.bhv, w.bcv));
-    const int pmax = w.panels < kRankPanels ? w.panels : kRankPanels;
+    const int pmax = w.panels < kRankPanels / kRankBlocks ? w.panels : kRankPanels / kRankBlocks;
     const int cap = w.bpanel ? rank_cap(p, pmax, PW) : 0;
     if (w.bpanel && cap >= 1024) {
         // rank-compacted passes for the rows it takes, then the dense-array
         // kernel for the rest (B unsorted, or more A entries than threads)
         SPG_LAUNCH(p, K_NUM_DENSE32, s,
-                   k_num_dense_rank<<<sms * p->occ_num_rank, kD32Threads, rank_smem(p, pmax, PW), s>>>(
+                   k_num_dense_rank<<<sms * p->occ_num_rank, kRankThreads, rank_smem(p, pmax, PW), s>>>(
                        A, B, w.map, w.ctl, rptC, row_begin, colC, valC, NB_DENSE32_0,
                        NB_DENSE32_0 + NB_DENSE_N, 4, w.bpanel, w.panels, PW, pmax, cap,
                        w.rc_slot, w.rc_bits, w.rc_nslots, w.rc_wpr, w.bcv));
