@@ -745,17 +745,22 @@ __device__ __forceinline__ void stage_pairs(const unsigned* bm, int* rk, int* st
 // ms); a pass that still holds more is accumulated in word ranges of at
 // most `cap` entries.
 // two 512-thread blocks per SM, each with half of the SM's shared memory
-// (12 panels per pass, ~15K values), instead of one of 1024: one block's
-// barriers and scans overlap the other's walk (193.4 -> 181.1 ms)
+// (14 panels per pass, ~13K values), instead of one of 1024 (24 panels,
+// ~32K values): one block's barriers and scans overlap the other's walk
+// (193.4 -> 181.1 ms at 12 panels)
 constexpr int kRankThreads = 512;
 constexpr int kRankBlocks = 2;                    // per SM
-constexpr int kRankPanels = 24;       // 20 and 28 measured slower, 32 leaves too few values
-constexpr int kRankUnroll = 6;        // value expansion: 4 / 5 / 6 / 7 -> 205.6 / 203.3 / 199.6 / 210.9 ms
+// panels per pass (each block's share of the SM): 10 / 12 / 14 / 16 -> 182.1 /
+// 181.1 / 180.3 / 202.4 ms (16 leaves too few values)
+constexpr int kRankPanels = 14;
+// products per lane per step of the value expansion: 4 / 5 / 6 -> 186.8 /
+// 183.9 / 181.1 ms at 12 panels, 7 -> 189.5 ms at 14
+constexpr int kRankUnroll = 6;
 constexpr int kRankOccUnroll = 8;     // occupancy expansion items are one int
 // A entries a row of this kernel may have (more go to k_num_dense<0>): the
 // fp32 rule keeps dense rows to at most fp32_max_terms (167 by default)
-// entries, and a tile of 256 leaves ~15 KB more for values than one of
-// kD32Threads
+// entries, and a tile of 256 entries leaves more shared memory for values
+// than one entry per thread
 constexpr int kRankTileE = kRankTileEntries;
 
 // With a row bitmap cache, a row that holds a slot reads each pass's bitmap
@@ -1726,8 +1731,8 @@ void occupancy_numeric(spgemm_plan* p) {
         size_t smem;
         int* occ;
     } ks[] = {
-        {(const void*)k_num_dense_rank, kRankThreads,
-         rank_smem(p, kRankPanels / kRankBlocks, p->opts.panel_cols), &p->occ_num_rank},
+        {(const void*)k_num_dense_rank, kRankThreads, rank_smem(p, kRankPanels, p->opts.panel_cols),
+         &p->occ_num_rank},
         {(const void*)k_num_warp<float>, kWarpsPerBlockNW * 32, num_warp_smem(4), &p->occ_num_warp32},
         {(const void*)k_num_warp<double>, kWarpsPerBlockNW * 32, num_warp_smem(8), &p->occ_num_warp64},
         {(const void*)k_num_block<float, kBlockThreadsFull>, kBlockThreadsFull, num_block_smem(p, 4),
@@ -1872,7 +1877,7 @@ void launch_numeric(const spgemm_plan* p, const CsrDev& A, const CsrDev& B, cons
     const int PW = w.panel_cols;
     if (w.bhv && w.bpanel && B.nnz > 0)
         SPG_LAUNCH(p, K_HOT, s, k_pack_b<<<sms * 8, 256, 0, s>>>(B, w.bhot, w.bhv, w.bcv));
-    const int pmax = w.panels < kRankPanels / kRankBlocks ? w.panels : kRankPanels / kRankBlocks;
+    const int pmax = w.panels < kRankPanels ? w.panels : kRankPanels;
     const int cap = w.bpanel ? rank_cap(p, pmax, PW) : 0;
     if (w.bpanel && cap >= 1024) {
         // rank-compacted passes for the rows it takes, then the dense-array
