@@ -1304,9 +1304,9 @@ __device__ __forceinline__ int auto_splits(int q, int P) {
 constexpr int kHotrSlots = 2048;
 constexpr int kHotrStride = kHotrSlots + 1;   // copies of one slot in different banks
 // threads per block and products per warp step batch: with 1024 threads
-// (64 registers), unroll 2 / 3 / 4 measured 254 / 248 / 268 ms on the R-MAT
-// scale 20 product (4 spills); 768 x 4 / 512 x 6 / 512 x 8 (more registers,
-// fewer warps) 273 / 316 / 324 ms
+// (64 registers), unroll 2 / 3 / 4 measured 219.2 / 211.7 / 231.0 ms on the
+// R-MAT scale 20 product (earlier forms: 254 / 248 / 268 ms); 768 x 4 /
+// 512 x 6 / 512 x 8 (more registers, fewer warps) 273 / 316 / 324 ms
 #ifndef SPG_HOTR_THREADS
 #define SPG_HOTR_THREADS 1024
 #endif
