@@ -850,31 +850,64 @@ def run_ours(args):
                    torch.empty(C2_blocks[0][2].nnz, dtype=torch.float32).pin_memory()]
         d2h = sum(t.numel() * t.element_size() for t in host_rp + host_c2)
 
-        def e2e_step():
-            A.row_ptr.copy_(pin["rp"], non_blocking=True)
-            A.col.copy_(pin["col"], non_blocking=True)
-            A.val.copy_(pin["val"], non_blocking=True)
-            S.row_ptr.copy_(pin["srp"], non_blocking=True)
-            S.col.copy_(pin["scol"], non_blocking=True)
-            S.val.copy_(pin["sval"], non_blocking=True)
-            St.row_ptr.copy_(pin["trp"], non_blocking=True)
-            St.col.copy_(pin["tcol"], non_blocking=True)
-            St.val.copy_(pin["tval"], non_blocking=True)
-            step()
-            for hb, (_, _, Cb) in zip(host_rp, blocks):
-                hb.copy_(Cb.row_ptr, non_blocking=True)
-            C2 = C2_blocks[0][2]
-            host_c2[0].copy_(C2.row_ptr, non_blocking=True)
-            host_c2[1].copy_(C2.col, non_blocking=True)
-            host_c2[2].copy_(C2.val, non_blocking=True)
+        # two device copies of the operands: step i's inputs go into set i % 2
+        # on a copy stream while step i - 1 computes on the other set; each
+        # step's results are read back on the copy stream while the next step
+        # runs (its outputs are overwritten only after that read-back ends)
+        sets = [(A, S, St), (DeviceCSR.from_host(A_h, dev), DeviceCSR.from_host(S_h, dev),
+                             DeviceCSR.from_host(St_h, dev))]
+        copy_stream = torch.cuda.Stream(device=dev)
+        h2d_done = [torch.cuda.Event(), torch.cuda.Event()]
+        comp_done = [torch.cuda.Event(), torch.cuda.Event()]
+        rp_done, c2_done = torch.cuda.Event(), torch.cuda.Event()
 
-        e2e_step()
+        def upload(k):
+            Ad, Sd, Std = sets[k]
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(comp_done[k])        # set k's previous step has ended
+                for dst, src in ((Ad.row_ptr, "rp"), (Ad.col, "col"), (Ad.val, "val"),
+                                 (Sd.row_ptr, "srp"), (Sd.col, "scol"), (Sd.val, "sval"),
+                                 (Std.row_ptr, "trp"), (Std.col, "tcol"), (Std.val, "tval")):
+                    dst.copy_(pin[src], non_blocking=True)
+                h2d_done[k].record(copy_stream)
+
+        def run(i):
+            k = i % 2
+            Ad, Sd, Std = sets[k]
+            stream.wait_event(h2d_done[k])
+            stream.wait_event(rp_done)                      # the last step's row pointers are read
+            plan.spgemm_blocks(Ad, Ad, ws=ws_aa, out=blocks)
+            stream.wait_event(c2_done)                      # the last step's C(S^T A S) is read
+            plan_c.spgemm_blocks(Std, Ad, ws=ws_sa, out=T_blocks)
+            plan_c.spgemm_blocks(T, Sd, ws=ws_ts, out=C2_blocks)
+            comp_done[k].record(stream)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(comp_done[k])
+                for hb, (_, _, Cb) in zip(host_rp, blocks):
+                    hb.copy_(Cb.row_ptr, non_blocking=True)
+                rp_done.record(copy_stream)
+                C2 = C2_blocks[0][2]
+                host_c2[0].copy_(C2.row_ptr, non_blocking=True)
+                host_c2[1].copy_(C2.col, non_blocking=True)
+                host_c2[2].copy_(C2.val, non_blocking=True)
+                c2_done.record(copy_stream)
+
+        def e2e_steps(n, start=None):
+            if start is not None:
+                copy_stream.wait_event(start)               # no copy before the timed region
+            upload(0)
+            for i in range(n):
+                if i + 1 < n:
+                    upload((i + 1) % 2)
+                run(i)
+            stream.wait_event(c2_done)                      # the last read-back is inside
+
+        e2e_steps(2)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk_e2e:
             e0.record(stream)
-            for _ in range(args.steps):
-                e2e_step()
+            e2e_steps(args.steps, start=e0)
             e1.record(stream)
             barrier()
         ems = e0.elapsed_time(e1)
@@ -882,8 +915,10 @@ def run_ours(args):
         e2e = {"value": 2.0 * ip_step * world / (ems / args.steps / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "clocks": clk_e2e.summary(),
-               "note": "inputs copied from pinned host memory each step; C(S^T A S) and the "
-                       "row pointers of every A*A block read back (the A*A values stay in HBM)"}
+               "note": "inputs copied from pinned host memory each step (into one of two device "
+                       "copies of the operands, overlapped with the previous step); C(S^T A S) "
+                       "and the row pointers of every A*A block read back (the A*A values stay "
+                       "in HBM)"}
 
     patterns = None
     if rank == 0 and world == 1 and not args.no_patterns:
