@@ -204,7 +204,7 @@ class ClockSampler:
 # traffic; a kernel changed since its capture must drop out of this table.
 DRAM_BYTES_PER_PRODUCT = {
     # k_num_dense_hotr (rank-compacted fp64-bound tier with the row bitmap cache)
-    "num_dense64": (945.734656e6 + 343.006720e6) / 256228740,
+    "num_dense64": (911.744000e6 + 341.544192e6) / 256228740,
     # k_num_dense_rank (rank-compacted fp32 tier with the row bitmap cache)
     "num_dense32": (1087.925e6 + 1067.939e6) / 257686006,
 }

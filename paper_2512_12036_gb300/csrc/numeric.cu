@@ -1314,7 +1314,11 @@ __device__ __forceinline__ int auto_splits(int q, int P) {
     return sp < P ? sp : (P > 0 ? P : 1);
 }
 
-constexpr int kHotrSlots = 2048;
+// hot-column slots and value slots of a pass: 2048 / 20480, 1792 / 22528,
+// 1536 / 24576, 1024 / 28672 -> 211.3 / 206.5 / 204.7 / 222.1 ms (fewer
+// slots leave room for more values; too few cut passes at hot columns)
+constexpr int kHotrSlots = 1536;
+constexpr int kHotrCap = 24576;
 constexpr int kHotrStride = kHotrSlots + 1;   // copies of one slot in different banks
 // threads per block and products per warp step batch: with 1024 threads
 // (64 registers), unroll 2 / 3 / 4 measured 219.2 / 211.7 / 231.0 ms on the
@@ -1724,13 +1728,13 @@ void occupancy_numeric(spgemm_plan* p) {
         if (avail > p->smem_optin) avail = p->smem_optin;
         p->rank_budget = avail > fa.sharedSizeBytes ? avail - fa.sharedSizeBytes : 0;
     }
-    // rank-compacted fp64 tier: 20480 value slots (at least one panel), as
-    // many panels per pass as the rest of shared memory holds
+    // rank-compacted fp64 tier: kHotrCap value slots (at least one panel),
+    // as many panels per pass as the rest of shared memory holds
     {
         cudaFuncAttributes fa{};
         cudaFuncGetAttributes(&fa, (const void*)k_num_dense_hotr);
         const int pw = p->opts.panel_cols;
-        const int cap = pw > 20480 ? pw : 20480;
+        const int cap = pw > kHotrCap ? pw : kHotrCap;
         const size_t budget = p->smem_optin > fa.sharedSizeBytes ? p->smem_optin - fa.sharedSizeBytes : 0;
         const size_t base = hotr_smem(pw, 0, cap), per = (size_t)(pw / 32) * 8;
         p->hotr_cap = cap;
